@@ -1,0 +1,309 @@
+/*
+ * gr.h — C ABI of the GB300 frontier-traversal library.
+ *
+ * The library implements the data-parallel hot path of the frontier
+ * abstraction of Wang et al., "Gunrock: GPU Graph Analytics" (ACM TOPC 2017):
+ * the advance operator (Sec. 4.1, Sec. 5.1), the filter operator (Sec. 4.2,
+ * Sec. 5.2.1), and the two primitives they drive, breadth-first search with
+ * the direction-optimising pull step (Sec. 6.1, Sec. 5.1.4, Alg. 2) and
+ * single-source shortest paths with integer weights and a near/far priority
+ * queue (Sec. 3 example, Alg. 1, Sec. 5.1.5, Sec. 6.2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Graphs are CSR with int32 row offsets R (n+1 entries, R[0] = 0,
+ *    R[n] = m, non-decreasing) and int32 column indices C (m entries, each in
+ *    [0, n)), optionally uint32 weights W (m entries, each >= 1).
+ *  - Every pointer to per-vertex or per-edge data is a DEVICE pointer owned by
+ *    the caller unless stated otherwise; the library never frees it.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream.  Entry points are asynchronous on that stream unless marked
+ *    "synchronous".
+ *  - Results: unreachable vertices get depth -1, dist GR_INF_DIST (UINT32_MAX)
+ *    and pred -1; the source gets depth 0, dist 0, pred -1 (Alg. 1
+ *    Set_Problem_Data).
+ *  - Argument errors are returned synchronously.  Errors the GPU detects
+ *    while running (capacity exceeded, distance overflow, barrier timeout)
+ *    are recorded in a device status word of the workspace and reported by
+ *    gr_sync_status().  The library never traps or asserts on the device.
+ *  - Thread safety: a gr_graph is immutable after creation and may be shared
+ *    by concurrent calls; a gr_workspace must be used by one call at a time
+ *    (calls on different streams need different workspaces).
+ */
+#ifndef GR_H_
+#define GR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+typedef int32_t gr_status;
+#define GR_OK                 0
+#define GR_ERR_INVALID_ARG   -1  /* bad pointer, size, source or mode        */
+#define GR_ERR_OOM           -2  /* device allocation failed                  */
+#define GR_ERR_CUDA          -3  /* a CUDA runtime call failed                */
+#define GR_ERR_CAPACITY      -4  /* an output buffer was too small            */
+#define GR_ERR_OVERFLOW      -5  /* a distance does not fit below UINT32_MAX  */
+#define GR_ERR_TIMEOUT       -6  /* a device-side wait ran out of iterations  */
+#define GR_ERR_INVALID_GRAPH -7  /* CSR failed validation                     */
+#define GR_ERR_UNSUPPORTED   -8  /* mode not available for this graph         */
+
+#define GR_INF_DIST 0xFFFFFFFFu
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* gr_status_str(gr_status s);
+
+/* Library ABI version: (major << 16) | minor. */
+int32_t gr_version(void);
+
+/* ---- graph ------------------------------------------------------------- */
+typedef struct gr_graph gr_graph;
+typedef struct gr_workspace gr_workspace;
+
+/* gr_graph_create_csr flags */
+#define GR_BORROW    0u  /* keep the caller's device arrays (caller keeps them alive) */
+#define GR_COPY      1u  /* copy R, C, W into device memory the graph owns            */
+#define GR_SYMMETRIC 2u  /* caller asserts (u,v) in E => (v,u) in E with equal weight;
+                            verified on the device; enables the pull step         */
+
+/*
+ * Create a graph handle over a device CSR (Sec. 5.4: CSR row offsets R and
+ * column indices C; per-edge data as a structure of arrays).
+ *   n >= 0 vertices, m >= 0 directed entries, n and m below 2^31.
+ *   row_offsets: device int32[n+1]; cols: device int32[m];
+ *   weights: device uint32[m] or NULL (needed only by SSSP).
+ * Validates on the device and is synchronous on `stream`: returns
+ * GR_ERR_INVALID_GRAPH if R[0] != 0, R[n] != m, R decreases, a column is
+ * outside [0, n), a weight is 0, or (with GR_SYMMETRIC) some row is unsorted
+ * or some edge has no reverse edge of equal weight.
+ * On success *out owns a default workspace for BFS and SSSP.
+ */
+gr_status gr_graph_create_csr(int32_t n, int64_t m, const int32_t* row_offsets,
+                              const int32_t* cols, const uint32_t* weights, uint32_t flags,
+                              void* stream, gr_graph** out);
+
+/* Destroy a graph and its default workspace (synchronises the device). */
+gr_status gr_graph_destroy(gr_graph* g);
+
+/* Sizes and flags of a graph; any output pointer may be NULL.  Host call. */
+gr_status gr_graph_info(const gr_graph* g, int32_t* n, int64_t* m, uint32_t* flags,
+                        int32_t* max_degree);
+
+/* Operations for footprint queries and workspaces. */
+#define GR_OP_BFS  1
+#define GR_OP_SSSP 2
+
+/*
+ * Device bytes one query of `op` needs beyond the graph itself (the
+ * workspace size).  Feeds admission control in the paper's footprint model
+ * alpha*|E| + beta*|V| (Sec. 7, memory usage discussion).  Host call.
+ */
+gr_status gr_graph_footprint(const gr_graph* g, int32_t op, size_t* bytes_per_query);
+
+/*
+ * Per-query scratch (frontier queues, bitmaps, packed SSSP keys, counters,
+ * status word).  `ops` is a mask of GR_OP_BFS | GR_OP_SSSP.  Synchronous.
+ */
+gr_status gr_workspace_create(const gr_graph* g, int32_t ops, gr_workspace** out);
+gr_status gr_workspace_destroy(gr_workspace* ws);
+
+/*
+ * Wait for `stream`, then read and clear the status word of `ws` (NULL = the
+ * graph's default workspace).  Returns GR_OK or the first device-detected
+ * error since the last call (GR_ERR_CAPACITY, GR_ERR_OVERFLOW,
+ * GR_ERR_TIMEOUT).  Synchronous.
+ */
+gr_status gr_sync_status(const gr_graph* g, gr_workspace* ws, void* stream);
+
+/*
+ * Work counters of the last gr_bfs / gr_sssp run on a workspace (the
+ * quantities behind the paper's traversal-throughput accounting, Sec. 7
+ * "Measurement methodology"):
+ *   levels:   BFS levels, or SSSP near/far steps, executed;
+ *   edges:    column entries read (edges inspected; pull levels stop early);
+ *   vertices: rows opened (frontier rows and edge chunks expanded, pull
+ *             candidates scanned, far-pile entries re-examined);
+ *   updates:  vertices discovered (BFS) or successful relaxations (SSSP).
+ */
+typedef struct gr_run_stats {
+  int32_t levels;
+  int32_t reserved;
+  int64_t edges;
+  int64_t vertices;
+  int64_t updates;
+} gr_run_stats;
+
+/* Wait for `stream` and read the counters of `ws` (NULL = default).  Synchronous. */
+gr_status gr_last_run_stats(const gr_graph* g, gr_workspace* ws, gr_run_stats* out, void* stream);
+
+/* ---- operator state ---------------------------------------------------- */
+
+/*
+ * State of the BFS visit functor (Sec. 6.1: set depth and predecessor on
+ * discovery).  All pointers are device pointers of n entries.
+ *   depth: int32, -1 = unvisited.  pred: int32 or NULL.
+ *   level: depth of the input frontier; discovered vertices get level + 1.
+ */
+typedef struct gr_bfs_state {
+  int32_t* depth;
+  int32_t* pred;
+  int32_t level;
+} gr_bfs_state;
+
+/*
+ * State of the SSSP relax functor (Alg. 1 Update_Label / Set_Pred).  The
+ * label and predecessor of v live together in one packed 64-bit key
+ *   key[v] = ((uint64_t)dist << 32) | (uint32_t)pred
+ * so that one 64-bit atomicMin updates both consistently; the result is the
+ * smallest (dist, pred) pair offered, i.e. the minimum-id tight predecessor.
+ * Unreached: key = UINT64_MAX (dist UINT32_MAX, pred -1).
+ *   threshold: near/far split point for GR_FILTER_NEAR_FAR (dist < threshold
+ *   is near).
+ */
+typedef struct gr_sssp_state {
+  uint64_t* key;
+  uint32_t threshold;
+} gr_sssp_state;
+
+/* ---- advance (Sec. 4.1, Sec. 5.1) --------------------------------------- */
+
+/* mode bits */
+#define GR_V2V       0  /* output vertex ids                                    */
+#define GR_V2E       1  /* output edge ids (positions in C)                     */
+#define GR_PUSH      0  /* expand the neighbour lists of the input frontier     */
+#define GR_PULL      2  /* input = candidate (unvisited) vertices; Alg. 2       */
+#define GR_ORDERED   0  /* output in the canonical order of the degree scan     */
+#define GR_UNORDERED 4  /* any order (faster, atomics for placement)            */
+#define GR_IDEMPOTENT 8 /* BFS visit without atomics; duplicates allowed        */
+
+/* functors fused into the operator (Sec. 5.3) */
+#define GR_FN_NONE       0  /* plain expansion                                  */
+#define GR_FN_BFS_VISIT  1  /* state = gr_bfs_state*                            */
+#define GR_FN_SSSP_RELAX 2  /* state = gr_sssp_state*                           */
+
+/*
+ * One advance step: in (device int32[in_len]) -> out (device int32[out_cap]).
+ *   in_len: host count of input items; if in_len_dev is not NULL the count
+ *   is read on the device from *in_len_dev and in_len is its upper bound.
+ *   out_len: device int64*, receives the number of items produced.  If that
+ *   number exceeds out_cap, only out_cap items are written, *out_len still
+ *   receives the full count and the status word records GR_ERR_CAPACITY.
+ *
+ * GR_FN_NONE + GR_PUSH: out is the concatenation, in input order, of each
+ *   input vertex's neighbour list (V2V) or edge-id range (V2E); with
+ *   GR_UNORDERED the same multiset in any order.  Output-balanced: every
+ *   CTA writes an equal slice of the output (Sec. 5.1.3, load balance over
+ *   the output frontier).
+ * GR_FN_BFS_VISIT + GR_PUSH: for every edge (u, v) of the input, v with
+ *   depth -1 gets depth = level + 1 and pred = u, and is emitted once
+ *   (atomic claim); with GR_IDEMPOTENT the claim is a plain check-and-set
+ *   and v may be emitted more than once (Sec. 5.2.1).  Output order is
+ *   unspecified.  State must be gr_bfs_state*.
+ * GR_FN_BFS_VISIT + GR_PULL: each input vertex v with depth -1 scans its
+ *   row in order and takes the first neighbour u with depth == level as
+ *   parent (Alg. 2 Reverse_Advance); activated vertices are emitted in input
+ *   order.  Requires a GR_SYMMETRIC graph.
+ * GR_FN_SSSP_RELAX + GR_PUSH: for every edge (u, v, w) of the input with
+ *   dist(u) finite, atomicMin(key[v], pack(dist(u) + w, u)); every v whose
+ *   distance strictly dropped is emitted (possibly more than once).  Needs
+ *   weights.  A sum >= UINT32_MAX is dropped; if its target is still
+ *   unreached the status word records GR_ERR_OVERFLOW.
+ */
+gr_status gr_advance(const gr_graph* g, const int32_t* in, int64_t in_len,
+                     const int64_t* in_len_dev, int32_t mode, int32_t functor, const void* state,
+                     int32_t* out, int64_t out_cap, int64_t* out_len, void* stream);
+
+/* ---- filter (Sec. 4.2) -------------------------------------------------- */
+
+#define GR_FILTER_EXACT_UNIQUE 0 /* first occurrence of each id in [0,n), input order */
+#define GR_FILTER_CULL         1 /* inexact: every valid id at least once, no new ids  */
+#define GR_FILTER_UNVISITED    2 /* ignore `in`: all v with depth -1, ascending        */
+#define GR_FILTER_NEAR_FAR     3 /* stable split by dist < threshold (Sec. 5.1.5)      */
+
+/*
+ * One filter step: in (device int32[in_len]) -> out (+ far for NEAR_FAR).
+ * Items outside [0, n) are dropped by every mode.
+ *   EXACT_UNIQUE: exact stream compaction (global scan and scatter).
+ *   CULL: the inexact "uniquification" of Sec. 4.2 / Sec. 5.2.1: out holds
+ *     every valid input id at least once and no id more often than the
+ *     input does; order unspecified.
+ *   UNVISITED: state = gr_bfs_state*; in is ignored (may be NULL);
+ *     out = { v : depth[v] == -1 } ascending (Alg. 2
+ *     GenerateUnvisitedFrontier).
+ *   NEAR_FAR: state = gr_sssp_state*; near items (dist < threshold) go to
+ *     out, the rest to far, both in input order.  far/far_cap/far_len are
+ *     required for this mode only.
+ * Lengths/capacities behave as in gr_advance.  Scratch comes from the
+ * graph's default workspace, so concurrent filters on one graph must use
+ * distinct streams serialised by the caller.
+ */
+gr_status gr_filter(const gr_graph* g, const int32_t* in, int64_t in_len,
+                    const int64_t* in_len_dev, int32_t mode, const void* state, int32_t* out,
+                    int64_t out_cap, int64_t* out_len, int32_t* far, int64_t far_cap,
+                    int64_t* far_len, void* stream);
+
+/* ---- BFS (Sec. 6.1, Sec. 5.1.4) ----------------------------------------- */
+
+#define GR_DIR_AUTO 0  /* direction-optimising push/pull (Alg. 2, Eq. 5-6)     */
+#define GR_DIR_PUSH 1  /* push only                                            */
+#define GR_DIR_PULL 2  /* pull whenever the graph allows it (testing)          */
+
+typedef struct gr_bfs_opts {
+  int32_t direction;     /* GR_DIR_*                                            */
+  float do_a;            /* push -> pull when m_f > m_u * do_a (Eq. 5)          */
+  float do_b;            /* pull -> push when m_f < m_u * do_b (Eq. 6)          */
+  int32_t big_degree;    /* rows at least this long are split into edge chunks
+                            shared by the whole grid; 0 = library default     */
+  int32_t blocks_per_sm; /* persistent grid = blocks_per_sm * SMs; 0 = max    */
+  uint32_t spin_limit;   /* grid-barrier wait budget in polls; 0 = default    */
+  gr_workspace* ws;      /* NULL = the graph's default workspace              */
+  int32_t* level_stats;  /* optional device int32[3*max_levels]: per level
+                            (frontier size, direction, edges checked)        */
+  int32_t max_levels;    /* capacity of level_stats in levels                 */
+} gr_bfs_opts;
+
+/* Fill *o with the library defaults. */
+void gr_bfs_opts_default(gr_bfs_opts* o);
+
+/*
+ * Breadth-first search from src: depth[v] = fewest edges on a path src -> v
+ * (device int32[n]), pred[v] = a parent one level up (device int32[n] or
+ * NULL).  One persistent kernel runs the whole level loop on the device
+ * (no per-level host round trip, Sec. 5.3).  opts may be NULL.
+ */
+gr_status gr_bfs(const gr_graph* g, int32_t src, int32_t* depth, int32_t* pred,
+                 const gr_bfs_opts* opts, void* stream);
+
+/* ---- SSSP (Sec. 3 example, Alg. 1, Sec. 5.1.5, Sec. 6.2) ---------------- */
+
+typedef struct gr_sssp_opts {
+  uint32_t delta;        /* near/far bucket width; 0 = derived from the graph */
+  int32_t big_degree;    /* as in gr_bfs_opts                                  */
+  int32_t blocks_per_sm; /* as in gr_bfs_opts                                  */
+  uint32_t spin_limit;   /* as in gr_bfs_opts                                  */
+  gr_workspace* ws;      /* NULL = the graph's default workspace              */
+} gr_sssp_opts;
+
+void gr_sssp_opts_default(gr_sssp_opts* o);
+
+/*
+ * Single-source shortest paths from src over the graph's weights:
+ * dist[v] = minimum path weight (device uint32[n], GR_INF_DIST if
+ * unreachable), pred[v] = the smallest-id tight predecessor (device int32[n]
+ * or NULL).  Label-correcting advance/filter iterations with a two-level
+ * near/far priority queue; one persistent kernel.  Needs weights.  If some
+ * reachable vertex's shortest distance is >= UINT32_MAX the status word
+ * records GR_ERR_OVERFLOW (such vertices are left at GR_INF_DIST).
+ */
+gr_status gr_sssp(const gr_graph* g, int32_t src, uint32_t* dist, int32_t* pred,
+                  const gr_sssp_opts* opts, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GR_H_ */

@@ -1,0 +1,578 @@
+// gr_ops.cu — the standalone advance and filter operators (gr_advance, gr_filter).
+//
+// Advance (Sec. 4.1, Fig. "advance"): a prefix-sum of the input degrees gives
+// every input item its output offset; the load balancer then hands every
+// warp 32 consecutive OUTPUT positions (load balance over the output
+// frontier, Sec. 5.1.3), and each lane finds the input item owning its
+// position by a sorted search in the scanned offsets.
+//
+// Filter (Sec. 4.2, Fig. "filter"): exact modes are a global scan and
+// scatter (stable compaction); CULL is the inexact "uniquification" of
+// Sec. 5.2.1 done with a claim bitmap.
+#include <climits>
+
+#include "gr_internal.cuh"
+
+namespace {
+
+constexpr int T = GR_OPS_THREADS;
+constexpr int ITEMS = GR_SCAN_ITEMS;
+constexpr int TILE = GR_SCAN_TILE;
+
+__device__ __forceinline__ int64_t eff_len(const int64_t* len_dev, int64_t len_host) {
+  if (!len_dev) return len_host;
+  int64_t l = *len_dev;
+  return l < 0 ? 0 : (l < len_host ? l : len_host);
+}
+
+// Exclusive block scan of a 64-bit value over NT threads; *total gets the block sum.
+template <int NT>
+__device__ __forceinline__ long long block_excl_scan(long long x, long long* total) {
+  __shared__ long long warp_tot[NT / 32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    long long y = __shfl_up_sync(GR_FULL_MASK, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    long long t = lane < NT / 32 ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      long long y = __shfl_up_sync(GR_FULL_MASK, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < NT / 32) warp_tot[lane] = t;
+  }
+  __syncthreads();
+  long long base = wid ? warp_tot[wid - 1] : 0;
+  *total = warp_tot[NT / 32 - 1];
+  __syncthreads();
+  return base + incl - x;
+}
+
+// 64-bit warp-aggregated append into a user buffer with a 64-bit counter.
+__device__ __forceinline__ void warp_append64(int32_t* out, unsigned long long* len, int64_t cap,
+                                              bool take, int32_t v, int lane, int* status) {
+  unsigned mask = __ballot_sync(GR_FULL_MASK, take);
+  if (mask == 0) return;
+  int leader = __ffs(mask) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(len, (unsigned long long)__popc(mask));
+  base = __shfl_sync(GR_FULL_MASK, base, leader);
+  if (take) {
+    long long pos = (long long)base + __popc(mask & ((1u << lane) - 1u));
+    if (pos < cap) out[pos] = v;
+    else gr_set_status(status, GR_ERR_CAPACITY);
+  }
+}
+
+// Single-CTA exclusive scan of `count` block sums in place (two interleaved
+// arrays when `pairs`), total(s) to tot[0] (and tot[1]).
+__global__ void scan_block_sums(long long* sums, int64_t count, int pairs, long long* tot) {
+  __shared__ long long carry[2];
+  int64_t per = (count + blockDim.x - 1) / blockDim.x;
+  int64_t b0 = threadIdx.x * per, b1 = min(b0 + per, count);
+  for (int k = 0; k < (pairs ? 2 : 1); ++k) {
+    long long* a = sums + k * (GR_MAX_SCAN_BLOCKS / 2);
+    long long s = 0;
+    for (int64_t i = b0; i < b1; ++i) s += a[i];
+    long long total;
+    long long off = block_excl_scan<1024>(s, &total);
+    for (int64_t i = b0; i < b1; ++i) {
+      long long x = a[i];
+      a[i] = off;
+      off += x;
+    }
+    if (threadIdx.x == 0) carry[k] = total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    tot[0] = carry[0];
+    if (pairs) tot[1] = carry[1];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// advance: degree scan
+
+__global__ void adv_degree_tiles(const int32_t* __restrict__ R, const int32_t* __restrict__ in,
+                                 int64_t len_host, const int64_t* len_dev, int32_t n,
+                                 long long* item_off, long long* block_sums, int* status) {
+  int64_t len = eff_len(len_dev, len_host);
+  int64_t base = (int64_t)blockIdx.x * TILE + (int64_t)threadIdx.x * ITEMS;
+  long long d[ITEMS];
+  long long s = 0;
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    int64_t i = base + k;
+    d[k] = 0;
+    if (i < len) {
+      int u = in[i];
+      if (u >= 0 && u < n) d[k] = R[u + 1] - R[u];
+      else gr_set_status(status, GR_ERR_INVALID_ARG);
+    }
+    s += d[k];
+  }
+  long long total;
+  long long off = block_excl_scan<T>(s, &total);
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    int64_t i = base + k;
+    if (i < len) item_off[i] = off;
+    off += d[k];
+  }
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+__device__ __forceinline__ long long item_offset(const long long* item_off,
+                                                 const long long* block_sums, int64_t i) {
+  return block_sums[i / TILE] + item_off[i];
+}
+
+// Largest i in [lo, hi] with offset(i) <= p (offsets are non-decreasing).
+__device__ __forceinline__ int64_t search_item(const long long* item_off,
+                                               const long long* block_sums, int64_t lo,
+                                               int64_t hi, long long p) {
+  while (lo < hi) {
+    int64_t mid = lo + ((hi - lo + 1) >> 1);
+    if (item_offset(item_off, block_sums, mid) <= p) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+enum { FN_NONE_ORDERED = 0, FN_NONE_EDGES = 1, FN_BFS = 2, FN_BFS_IDEM = 3, FN_RELAX = 4 };
+
+struct ExpandArgs {
+  const int32_t* R;
+  const int32_t* C;
+  const uint32_t* W;
+  const int32_t* in;
+  int64_t len_host;
+  const int64_t* len_dev;
+  const long long* item_off;
+  const long long* block_sums;
+  const long long* total;
+  int32_t* out;
+  int64_t cap;
+  unsigned long long* out_len;
+  int* status;
+  // functor state
+  int32_t* depth;
+  int32_t* pred;
+  int32_t level;
+  unsigned long long* key;
+};
+
+// Output-balanced expansion: warp w owns output positions [32w, 32w + 32).
+template <int FN>
+__global__ void adv_expand(ExpandArgs a) {
+  int64_t len = eff_len(a.len_dev, a.len_host);
+  long long total = *a.total;
+  int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  long long limit = total;
+  if (FN == FN_NONE_ORDERED || FN == FN_NONE_EDGES) limit = total < a.cap ? total : a.cap;
+  for (long long p0 = warp * 32; p0 < limit; p0 += nwarps * 32) {
+    // narrow the search range with the warp's first and last positions
+    long long plast = min(p0 + 31, limit - 1);
+    int64_t lo = 0, hi = 0;
+    if (lane == 0) lo = search_item(a.item_off, a.block_sums, 0, len - 1, p0);
+    if (lane == 31) hi = search_item(a.item_off, a.block_sums, 0, len - 1, plast);
+    lo = __shfl_sync(GR_FULL_MASK, lo, 0);
+    hi = __shfl_sync(GR_FULL_MASK, hi, 31);
+    long long p = p0 + lane;
+    bool active = p < limit;
+    int32_t v = 0, u = 0;
+    int e = 0;
+    if (active) {
+      int64_t i = search_item(a.item_off, a.block_sums, lo, hi, p);
+      u = a.in[i];
+      e = a.R[u] + (int)(p - item_offset(a.item_off, a.block_sums, i));
+      v = __ldg(a.C + e);
+    }
+    if (FN == FN_NONE_ORDERED) {
+      if (active) a.out[p] = v;
+    } else if (FN == FN_NONE_EDGES) {
+      if (active) a.out[p] = e;
+    } else if (FN == FN_BFS || FN == FN_BFS_IDEM) {
+      bool won = false;
+      if (active && a.depth[v] == -1) {
+        if (FN == FN_BFS) {
+          won = atomicCAS(&a.depth[v], -1, a.level + 1) == -1;
+        } else {
+          a.depth[v] = a.level + 1;
+          won = true;
+        }
+        if (won && a.pred) a.pred[v] = u;
+      }
+      warp_append64(a.out, a.out_len, a.cap, won, v, lane, a.status);
+    } else {  // FN_RELAX
+      bool improved = false;
+      if (active) {
+        unsigned long long ku = a.key[u];
+        unsigned du = (unsigned)(ku >> 32);
+        if (du != GR_INF_DIST) {
+          unsigned long long nd = (unsigned long long)du + a.W[e];
+          if (nd >= (unsigned long long)GR_INF_DIST) {
+            // an unrepresentable candidate matters only for an unreached target
+            if ((a.key[v] >> 32) == GR_INF_DIST) gr_set_status(a.status, GR_ERR_OVERFLOW);
+          } else {
+            unsigned long long cand = (nd << 32) | (unsigned)u;
+            if (cand < a.key[v]) {
+              unsigned long long old = atomicMin(&a.key[v], cand);
+              improved = (old >> 32) > nd;
+            }
+          }
+        }
+      }
+      warp_append64(a.out, a.out_len, a.cap, improved, v, lane, a.status);
+    }
+  }
+}
+
+__global__ void write_len_and_check(const long long* total, unsigned long long* out_len,
+                                    int64_t cap, int* status) {
+  long long t = *total;
+  *out_len = (unsigned long long)t;
+  if (t > cap) gr_set_status(status, GR_ERR_CAPACITY);
+}
+
+// ---------------------------------------------------------------------------
+// ordered compaction (filters and the pull advance)
+
+enum { CL_UNIQUE = 0, CL_UNVISITED = 1, CL_NEAR_FAR = 2, CL_PULL = 3 };
+
+struct CompactArgs {
+  int32_t n;
+  const int32_t* R;
+  const int32_t* C;
+  const int32_t* in;
+  int64_t len_host;
+  const int64_t* len_dev;
+  long long* block_sums;   // two interleaved halves for two-output modes
+  const long long* totals; // device scan totals
+  int32_t* out;
+  int64_t cap;
+  unsigned long long* out_len;
+  int32_t* far;
+  int64_t far_cap;
+  unsigned long long* far_len;
+  int* status;
+  int32_t* first_idx;
+  int32_t* depth;
+  int32_t* pred;
+  int32_t level;
+  const unsigned long long* key;
+  uint32_t threshold;
+  int32_t* tags;
+};
+
+// Class of item i: 0 dropped, 1 to out, 2 to far.  In the count pass
+// (SCATTER == false) CL_PULL does the neighbour scan and records the found
+// parent in tags[i]; the scatter pass reads it back.
+template <int CL, bool SCATTER>
+__device__ __forceinline__ int classify(const CompactArgs& a, int64_t i) {
+  if (CL == CL_UNVISITED) return a.depth[i] == -1 ? 1 : 0;
+  int32_t v = a.in[i];
+  if (v < 0 || v >= a.n) return 0;
+  if (CL == CL_UNIQUE) {
+    if (a.first_idx[v] != (int32_t)i) return 0;
+    if (SCATTER) a.first_idx[v] = INT32_MAX;  // leave the scratch clean
+    return 1;
+  }
+  if (CL == CL_NEAR_FAR) return (unsigned)(a.key[v] >> 32) < a.threshold ? 1 : 2;
+  // CL_PULL
+  if (SCATTER) return a.tags[i] >= 0 ? 1 : 0;
+  int32_t found = -1;
+  if (a.depth[v] == -1) {
+    for (int e = a.R[v]; e < a.R[v + 1]; ++e) {
+      int32_t u = __ldg(a.C + e);
+      if (a.depth[u] == a.level) { found = u; break; }
+    }
+  }
+  a.tags[i] = found;
+  return found >= 0 ? 1 : 0;
+}
+
+template <int CL>
+__global__ void compact_count(CompactArgs a) {
+  int64_t len = CL == CL_UNVISITED ? a.n : eff_len(a.len_dev, a.len_host);
+  int64_t base = (int64_t)blockIdx.x * TILE + (int64_t)threadIdx.x * ITEMS;
+  long long c1 = 0, c2 = 0;
+  for (int k = 0; k < ITEMS; ++k) {
+    int64_t i = base + k;
+    if (i >= len) break;
+    int c = classify<CL, false>(a, i);
+    c1 += c == 1;
+    c2 += c == 2;
+  }
+  long long t1, t2;
+  block_excl_scan<T>(c1, &t1);
+  if (CL == CL_NEAR_FAR) block_excl_scan<T>(c2, &t2);
+  if (threadIdx.x == 0) {
+    a.block_sums[blockIdx.x] = t1;
+    if (CL == CL_NEAR_FAR) a.block_sums[GR_MAX_SCAN_BLOCKS / 2 + blockIdx.x] = t2;
+  }
+}
+
+template <int CL>
+__global__ void compact_scatter(CompactArgs a) {
+  int64_t len = CL == CL_UNVISITED ? a.n : eff_len(a.len_dev, a.len_host);
+  int64_t base = (int64_t)blockIdx.x * TILE + (int64_t)threadIdx.x * ITEMS;
+  unsigned char cls[ITEMS];
+  long long c1 = 0, c2 = 0;
+  for (int k = 0; k < ITEMS; ++k) {
+    int64_t i = base + k;
+    cls[k] = 0;
+    if (i < len) cls[k] = (unsigned char)classify<CL, true>(a, i);
+    c1 += cls[k] == 1;
+    c2 += cls[k] == 2;
+  }
+  long long t1, t2 = 0;
+  long long o1 = block_excl_scan<T>(c1, &t1) + a.block_sums[blockIdx.x];
+  long long o2 = 0;
+  if (CL == CL_NEAR_FAR)
+    o2 = block_excl_scan<T>(c2, &t2) + a.block_sums[GR_MAX_SCAN_BLOCKS / 2 + blockIdx.x];
+  for (int k = 0; k < ITEMS; ++k) {
+    int64_t i = base + k;
+    if (cls[k] == 1) {
+      int32_t v = CL == CL_UNVISITED ? (int32_t)i : a.in[i];
+      if (o1 < a.cap) a.out[o1] = v;
+      if (CL == CL_PULL) {
+        a.depth[v] = a.level + 1;
+        if (a.pred) a.pred[v] = a.tags[i];
+      }
+      ++o1;
+    } else if (cls[k] == 2) {
+      if (o2 < a.far_cap) a.far[o2] = a.in[i];
+      ++o2;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    long long tot1 = a.totals[0];
+    *a.out_len = (unsigned long long)tot1;
+    if (tot1 > a.cap) gr_set_status(a.status, GR_ERR_CAPACITY);
+    if (CL == CL_NEAR_FAR) {
+      long long tot2 = a.totals[1];
+      *a.far_len = (unsigned long long)tot2;
+      if (tot2 > a.far_cap) gr_set_status(a.status, GR_ERR_CAPACITY);
+    }
+  }
+}
+
+__global__ void unique_mark_first(const int32_t* in, int64_t len_host, const int64_t* len_dev,
+                                  int32_t n, int32_t* first_idx) {
+  int64_t len = eff_len(len_dev, len_host);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v = in[i];
+    if (v >= 0 && v < n) atomicMin(&first_idx[v], (int32_t)i);
+  }
+}
+
+// CULL: claim each id once in a bitmap; emit the claimants (order unspecified).
+__global__ void cull_claim(const int32_t* in, int64_t len_host, const int64_t* len_dev, int32_t n,
+                           uint32_t* claim, int32_t* out, int64_t cap,
+                           unsigned long long* out_len, int* status) {
+  int64_t len = eff_len(len_dev, len_host);
+  int lane = threadIdx.x & 31;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < len; i0 += stride) {
+    int64_t i = i0 + threadIdx.x;
+    bool take = false;
+    int32_t v = 0;
+    if (i < len) {
+      v = in[i];
+      if (v >= 0 && v < n) {
+        uint32_t bit = 1u << (v & 31);
+        if (!(claim[v >> 5] & bit)) take = !(atomicOr(&claim[v >> 5], bit) & bit);
+      }
+    }
+    warp_append64(out, out_len, cap, take, v, lane, status);
+  }
+}
+
+__global__ void cull_release(const int32_t* out, const unsigned long long* out_len, int64_t cap,
+                             uint32_t* claim) {
+  long long len = (long long)*out_len;
+  if (len > cap) len = cap;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x) {
+    int32_t v = out[i];
+    atomicAnd(&claim[v >> 5], ~(1u << (v & 31)));
+  }
+}
+
+int64_t tiles_for(int64_t len) { return (len + TILE - 1) / TILE; }
+
+}  // namespace
+
+#define GR_LAUNCH_CHECK()                                      \
+  do {                                                         \
+    if (cudaGetLastError() != cudaSuccess) return GR_ERR_CUDA; \
+  } while (0)
+
+extern "C" gr_status gr_advance(const gr_graph* g, const int32_t* in, int64_t in_len,
+                                const int64_t* in_len_dev, int32_t mode, int32_t functor,
+                                const void* state, int32_t* out, int64_t out_cap,
+                                int64_t* out_len, void* stream) {
+  if (!g || in_len < 0 || (in_len > 0 && !in) || out_cap < 0 || !out_len ||
+      (out_cap > 0 && !out) || (mode & ~(GR_V2E | GR_PULL | GR_UNORDERED | GR_IDEMPOTENT)) ||
+      functor < GR_FN_NONE || functor > GR_FN_SSSP_RELAX)
+    return GR_ERR_INVALID_ARG;
+  if (in_len >= INT32_MAX) return GR_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  gr_workspace* ws = g->ws_default;
+  unsigned long long* olen = (unsigned long long*)out_len;
+  int blocks_persist = g->num_sms * 8;
+
+  if (mode & GR_PULL) {
+    if (functor != GR_FN_BFS_VISIT || !state || (mode & GR_V2E)) return GR_ERR_INVALID_ARG;
+    if (!(g->flags & GR_SYMMETRIC)) return GR_ERR_UNSUPPORTED;
+    if (in_len > g->n) return GR_ERR_INVALID_ARG;
+    const gr_bfs_state* st = (const gr_bfs_state*)state;
+    if (!st->depth) return GR_ERR_INVALID_ARG;
+    if (in_len == 0) {
+      if (cudaMemsetAsync(out_len, 0, sizeof(int64_t), s) != cudaSuccess) return GR_ERR_CUDA;
+      return GR_OK;
+    }
+    CompactArgs a = {};
+    a.n = g->n; a.R = g->R; a.C = g->C; a.in = in; a.len_host = in_len; a.len_dev = in_len_dev;
+    a.block_sums = ws->block_sums; a.totals = ws->dev_len; a.out = out; a.cap = out_cap;
+    a.out_len = olen; a.status = ws->status; a.depth = st->depth; a.pred = st->pred;
+    a.level = st->level; a.tags = ws->tags;
+    int64_t tiles = tiles_for(in_len);
+    compact_count<CL_PULL><<<(unsigned)tiles, T, 0, s>>>(a);
+    scan_block_sums<<<1, 1024, 0, s>>>(ws->block_sums, tiles, 0, ws->dev_len);
+    compact_scatter<CL_PULL><<<(unsigned)tiles, T, 0, s>>>(a);
+    GR_LAUNCH_CHECK();
+    return GR_OK;
+  }
+
+  int fn;
+  if (functor == GR_FN_NONE) fn = (mode & GR_V2E) ? FN_NONE_EDGES : FN_NONE_ORDERED;
+  else if (functor == GR_FN_BFS_VISIT) fn = (mode & GR_IDEMPOTENT) ? FN_BFS_IDEM : FN_BFS;
+  else fn = FN_RELAX;
+  if (fn >= FN_BFS && ((mode & GR_V2E) || !state)) return GR_ERR_INVALID_ARG;
+  if (fn == FN_RELAX && !g->W && g->m > 0) return GR_ERR_UNSUPPORTED;
+
+  if (in_len == 0) {
+    if (cudaMemsetAsync(out_len, 0, sizeof(int64_t), s) != cudaSuccess) return GR_ERR_CUDA;
+    return GR_OK;
+  }
+  // per-item output offsets: the workspace holds n + 1 of them; longer
+  // inputs (frontiers with repeated vertices) use a stream-ordered temporary.
+  long long* item_off = ws->item_off;
+  bool tmp_alloc = in_len > (int64_t)g->n + 1;
+  if (tmp_alloc &&
+      cudaMallocAsync((void**)&item_off, (size_t)in_len * sizeof(long long), s) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return GR_ERR_OOM;
+  }
+  int64_t tiles = tiles_for(in_len);
+  adv_degree_tiles<<<(unsigned)tiles, T, 0, s>>>(g->R, in, in_len, in_len_dev, g->n, item_off,
+                                                 ws->block_sums, ws->status);
+  scan_block_sums<<<1, 1024, 0, s>>>(ws->block_sums, tiles, 0, ws->dev_len);
+  ExpandArgs a = {};
+  a.R = g->R; a.C = g->C; a.W = g->W; a.in = in; a.len_host = in_len; a.len_dev = in_len_dev;
+  a.item_off = item_off; a.block_sums = ws->block_sums; a.total = ws->dev_len; a.out = out;
+  a.cap = out_cap; a.out_len = olen; a.status = ws->status;
+  if (fn == FN_BFS || fn == FN_BFS_IDEM) {
+    const gr_bfs_state* st = (const gr_bfs_state*)state;
+    if (!st->depth) return GR_ERR_INVALID_ARG;
+    a.depth = st->depth; a.pred = st->pred; a.level = st->level;
+  } else if (fn == FN_RELAX) {
+    const gr_sssp_state* st = (const gr_sssp_state*)state;
+    if (!st->key) return GR_ERR_INVALID_ARG;
+    a.key = (unsigned long long*)st->key;
+  }
+  if (fn == FN_NONE_ORDERED || fn == FN_NONE_EDGES) {
+    write_len_and_check<<<1, 1, 0, s>>>(ws->dev_len, olen, out_cap, ws->status);
+  } else if (cudaMemsetAsync(out_len, 0, sizeof(int64_t), s) != cudaSuccess) {
+    return GR_ERR_CUDA;
+  }
+  switch (fn) {
+    case FN_NONE_ORDERED: adv_expand<FN_NONE_ORDERED><<<blocks_persist, T, 0, s>>>(a); break;
+    case FN_NONE_EDGES: adv_expand<FN_NONE_EDGES><<<blocks_persist, T, 0, s>>>(a); break;
+    case FN_BFS: adv_expand<FN_BFS><<<blocks_persist, T, 0, s>>>(a); break;
+    case FN_BFS_IDEM: adv_expand<FN_BFS_IDEM><<<blocks_persist, T, 0, s>>>(a); break;
+    default: adv_expand<FN_RELAX><<<blocks_persist, T, 0, s>>>(a); break;
+  }
+  GR_LAUNCH_CHECK();
+  if (tmp_alloc && cudaFreeAsync(item_off, s) != cudaSuccess) return GR_ERR_CUDA;
+  return GR_OK;
+}
+
+extern "C" gr_status gr_filter(const gr_graph* g, const int32_t* in, int64_t in_len,
+                               const int64_t* in_len_dev, int32_t mode, const void* state,
+                               int32_t* out, int64_t out_cap, int64_t* out_len, int32_t* far,
+                               int64_t far_cap, int64_t* far_len, void* stream) {
+  if (!g || in_len < 0 || in_len >= INT32_MAX || out_cap < 0 || !out_len ||
+      (out_cap > 0 && !out) || mode < GR_FILTER_EXACT_UNIQUE || mode > GR_FILTER_NEAR_FAR)
+    return GR_ERR_INVALID_ARG;
+  if (mode != GR_FILTER_UNVISITED && in_len > 0 && !in) return GR_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  gr_workspace* ws = g->ws_default;
+  unsigned long long* olen = (unsigned long long*)out_len;
+  CompactArgs a = {};
+  a.n = g->n; a.R = g->R; a.C = g->C; a.in = in; a.len_host = in_len; a.len_dev = in_len_dev;
+  a.block_sums = ws->block_sums; a.totals = ws->dev_len; a.out = out; a.cap = out_cap;
+  a.out_len = olen; a.status = ws->status; a.first_idx = ws->first_idx;
+
+  if (mode == GR_FILTER_UNVISITED) {
+    const gr_bfs_state* st = (const gr_bfs_state*)state;
+    if (!st || !st->depth) return GR_ERR_INVALID_ARG;
+    a.depth = st->depth;
+    if (g->n == 0) return cudaMemsetAsync(out_len, 0, 8, s) == cudaSuccess ? GR_OK : GR_ERR_CUDA;
+    int64_t tiles = tiles_for(g->n);
+    compact_count<CL_UNVISITED><<<(unsigned)tiles, T, 0, s>>>(a);
+    scan_block_sums<<<1, 1024, 0, s>>>(ws->block_sums, tiles, 0, ws->dev_len);
+    compact_scatter<CL_UNVISITED><<<(unsigned)tiles, T, 0, s>>>(a);
+    GR_LAUNCH_CHECK();
+    return GR_OK;
+  }
+  if (mode == GR_FILTER_NEAR_FAR) {
+    const gr_sssp_state* st = (const gr_sssp_state*)state;
+    if (!st || !st->key || !far_len || (far_cap > 0 && !far) || far_cap < 0)
+      return GR_ERR_INVALID_ARG;
+    if (in_len == 0) {
+      if (cudaMemsetAsync(out_len, 0, 8, s) || cudaMemsetAsync(far_len, 0, 8, s))
+        return GR_ERR_CUDA;
+      return GR_OK;
+    }
+    if (tiles_for(in_len) > GR_MAX_SCAN_BLOCKS / 2) return GR_ERR_INVALID_ARG;
+    a.key = (const unsigned long long*)st->key;
+    a.threshold = st->threshold;
+    a.far = far; a.far_cap = far_cap; a.far_len = (unsigned long long*)far_len;
+    int64_t tiles = tiles_for(in_len);
+    compact_count<CL_NEAR_FAR><<<(unsigned)tiles, T, 0, s>>>(a);
+    scan_block_sums<<<1, 1024, 0, s>>>(ws->block_sums, tiles, 1, ws->dev_len);
+    compact_scatter<CL_NEAR_FAR><<<(unsigned)tiles, T, 0, s>>>(a);
+    GR_LAUNCH_CHECK();
+    return GR_OK;
+  }
+  if (in_len == 0)
+    return cudaMemsetAsync(out_len, 0, 8, s) == cudaSuccess ? GR_OK : GR_ERR_CUDA;
+  if (mode == GR_FILTER_EXACT_UNIQUE) {
+    int64_t tiles = tiles_for(in_len);
+    unique_mark_first<<<g->num_sms * 8, T, 0, s>>>(in, in_len, in_len_dev, g->n, ws->first_idx);
+    compact_count<CL_UNIQUE><<<(unsigned)tiles, T, 0, s>>>(a);
+    scan_block_sums<<<1, 1024, 0, s>>>(ws->block_sums, tiles, 0, ws->dev_len);
+    compact_scatter<CL_UNIQUE><<<(unsigned)tiles, T, 0, s>>>(a);
+    GR_LAUNCH_CHECK();
+    return GR_OK;
+  }
+  // GR_FILTER_CULL
+  if (cudaMemsetAsync(out_len, 0, 8, s) != cudaSuccess) return GR_ERR_CUDA;
+  cull_claim<<<g->num_sms * 8, T, 0, s>>>(in, in_len, in_len_dev, g->n, ws->claim, out, out_cap,
+                                          olen, ws->status);
+  cull_release<<<g->num_sms * 8, T, 0, s>>>(out, olen, out_cap, ws->claim);
+  GR_LAUNCH_CHECK();
+  return GR_OK;
+}

@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads without a GPU, and exports every symbol gr.h declares.
+
+No compute call is made here (this runs on machines without a GPU).
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gr.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(gr_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_1701_01170_gb300 import _build
+    try:
+        _build.nvcc()
+    except RuntimeError:
+        pytest.skip("nvcc not available")
+    return _build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("gr_graph_create_csr", "gr_advance", "gr_filter", "gr_bfs", "gr_sssp",
+                     "gr_sync_status", "gr_graph_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"declared in gr.h but not exported: {missing}"
+
+
+def test_exports_are_c_linkage(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r" T (gr_[a-z0-9_]+)$", out, flags=re.M))
+    assert set(declared_functions()) <= exported
+
+
+def test_status_strings_without_gpu(lib_path):
+    import paper_1701_01170_gb300 as gr
+    gr.load()
+    assert gr.status_str(gr.GR_OK) == "GR_OK"
+    assert gr.status_str(gr.GR_ERR_TIMEOUT) == "GR_ERR_TIMEOUT"
+    assert gr.status_str(-99) == "GR_ERR_UNKNOWN"
+    assert gr.gr_version() >> 16 == 1
+
+
+def test_option_struct_layouts_match_header(lib_path):
+    import paper_1701_01170_gb300 as gr
+    o = gr.bfs_opts()
+    assert o.direction == gr.GR_DIR_AUTO and o.big_degree > 0 and o.spin_limit > 0
+    s = gr.sssp_opts()
+    assert s.delta == 0 and s.big_degree > 0
+    assert ctypes.sizeof(gr.gr_bfs_opts) == 48
+    assert ctypes.sizeof(gr.gr_sssp_opts) == 24
+    assert ctypes.sizeof(gr.gr_bfs_state) == 24
+    assert ctypes.sizeof(gr.gr_sssp_state) == 16
+
+
+def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
+    import paper_1701_01170_gb300 as gr
+    from paper_1701_01170_gb300 import _build
+    monkeypatch.setattr(gr, "_lib", None)
+    monkeypatch.setattr(_build, "LIB", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        gr.load()

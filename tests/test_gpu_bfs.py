@@ -1,0 +1,204 @@
+"""GPU parity of gr_bfs (persistent direction-optimising BFS) against the CPU oracle.
+
+Depths must equal the oracle's bit for bit; predecessors must pass the BFS
+certificate (any valid BFS tree is a correct answer, Sec. 6.1).  Every
+direction policy and split threshold must give the same depths.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from _helpers import dev, host, star_plus, undirected
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gr():
+    import paper_1701_01170_gb300 as m
+    m.load()
+    return m
+
+
+def run_bfs(gr, G, src, **opts):
+    import torch
+    depth = torch.empty(G.n, dtype=torch.int32, device="cuda")
+    pred = torch.empty_like(depth)
+    o = gr.bfs_opts(**opts) if opts else None
+    gr.gr_bfs(G.handle, src, depth, pred, o)
+    st = G.sync_status()
+    assert st == gr.GR_OK, gr.status_str(st)
+    return host(depth), host(pred)
+
+
+def check(g, src, depth, pred):
+    want, _ = oracle.bfs(g.R, g.C, src)
+    assert np.array_equal(depth, want)
+    assert oracle.bfs_certificate(g.R, g.C, src, depth, pred) == 0
+
+
+@pytest.fixture(scope="module")
+def s16(gr):
+    g = gg.rmat(16, 16, seed=1)
+    return g, gr.Graph.from_csr(g)
+
+
+def test_config_s16_from_vertex0(gr, s16):
+    g, G = s16
+    d, p = run_bfs(gr, G, 0)
+    check(g, 0, d, p)
+
+
+@pytest.mark.parametrize("direction", [0, 1, 2])
+@pytest.mark.parametrize("big", [32, 100, 1024, 1 << 30])
+def test_directions_and_split_thresholds_agree(gr, s16, direction, big):
+    g, G = s16
+    for src in (0, 12345, int(gg.sources(g, 1, seed=9)[0])):
+        d, p = run_bfs(gr, G, src, direction=direction, big_degree=big)
+        check(g, src, d, p)
+
+
+@pytest.mark.parametrize("do_a,do_b", [(0.0, 0.0), (1e-4, 1e-6), (0.5, 0.1), (1e9, 0.0)])
+def test_switch_parameters_do_not_change_depths(gr, s16, do_a, do_b):
+    g, G = s16
+    d, p = run_bfs(gr, G, 0, do_a=do_a, do_b=do_b)
+    check(g, 0, d, p)
+
+
+def test_level_stats(gr, s16):
+    import torch
+    g, G = s16
+    stats = torch.full((3 * 64,), -7, dtype=torch.int32, device="cuda")
+    d, p = run_bfs(gr, G, 0, level_stats=stats.data_ptr(), max_levels=64)
+    check(g, 0, d, p)
+    s = host(stats).reshape(64, 3)
+    levels = int(d.max()) + 1
+    counts = np.bincount(d[d >= 0], minlength=levels)
+    assert np.array_equal(s[:levels, 0], counts)        # frontier size per level
+    deg = g.degrees()
+    for L in range(levels):                              # m_f per level = sum of degrees
+        assert s[L, 2] == min(int(deg[d == L].sum()), 2**31 - 1)
+
+
+def test_small_and_degenerate_graphs(gr):
+    cases = [
+        (undirected(1, np.zeros((0, 2))), 0),                  # single vertex, no edge
+        (undirected(5, [(0, 1), (2, 3)]), 4),                  # isolated source
+        (undirected(5, [(0, 1), (2, 3)]), 1),                  # two components
+        (undirected(2000, [(i, i + 1) for i in range(1999)]), 0),   # long path
+        (undirected(40, [(i, j) for i in range(40) for j in range(i + 1, 40)]), 3),  # K_40
+    ]
+    for deg in (31, 32, 33, 255, 256, 257, 1023, 1024, 1025, 5000):
+        cases.append((star_plus(deg), 0))
+        cases.append((star_plus(deg), 1))
+    for g, src in cases:
+        G = gr.Graph.from_csr(g)
+        for direction in (0, 1, 2):
+            for big in (32, 1024):
+                d, p = run_bfs(gr, G, src, direction=direction, big_degree=big)
+                check(g, src, d, p)
+        G.close()
+
+
+def test_directed_graph_push_only(gr):
+    rng = np.random.default_rng(3)
+    n = 3000
+    s, t = rng.integers(0, n, 20000), rng.integers(0, n, 20000)
+    keep = s != t
+    pairs = np.unique(np.stack([s[keep], t[keep]], 1), axis=0)
+    g = gg.directed(n, pairs[:, 0], pairs[:, 1])
+    G = gr.Graph.from_csr(g, symmetric=False)
+    d, p = run_bfs(gr, G, 0)
+    check(g, 0, d, p)
+    with pytest.raises(gr.GrError):
+        run_bfs(gr, G, 0, direction=gr.GR_DIR_PULL)
+
+
+def test_invalid_arguments_rejected(gr, s16):
+    import torch
+    g, G = s16
+    depth = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    for bad in (-1, g.n):
+        with pytest.raises(gr.GrError) as e:
+            gr.gr_bfs(G.handle, bad, depth)
+        assert e.value.status == gr.GR_ERR_INVALID_ARG
+
+
+def test_invalid_graphs_rejected(gr):
+    import torch
+    R = torch.tensor([0, 1, 2], dtype=torch.int32, device="cuda")
+    C = torch.tensor([1, 0], dtype=torch.int32, device="cuda")
+    bad_cases = [
+        (torch.tensor([0, 1, 3], dtype=torch.int32, device="cuda"), C, None, 0),  # R[n] != m
+        (torch.tensor([1, 1, 2], dtype=torch.int32, device="cuda"), C, None, 0),  # R[0] != 0
+        (R, torch.tensor([1, 2], dtype=torch.int32, device="cuda"), None, 0),     # col >= n
+        (R, torch.tensor([1, -1], dtype=torch.int32, device="cuda"), None, 0),    # col < 0
+        (R, C, torch.tensor([3, 0], dtype=torch.int32, device="cuda"), 0),        # zero weight
+        (R, C, torch.tensor([3, 4], dtype=torch.int32, device="cuda"), 2),        # asym weight
+        (R, torch.tensor([1, 1], dtype=torch.int32, device="cuda"), None, 2),     # asym edge
+    ]
+    for r, c, w, flags in bad_cases:
+        with pytest.raises(gr.GrError) as e:
+            gr.gr_graph_create_csr(2, 2, r, c, w, flags)
+        assert e.value.status == gr.GR_ERR_INVALID_GRAPH
+    h = gr.gr_graph_create_csr(2, 2, R, C, None, gr.GR_SYMMETRIC | gr.GR_COPY)
+    gr.gr_graph_destroy(h)
+
+
+def test_barrier_timeout_is_reported_and_recoverable(gr, s16):
+    import torch
+    g, G = s16
+    depth = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    seen = None
+    for _ in range(3):   # a budget of one poll runs out while other CTAs still work
+        gr.gr_bfs(G.handle, 0, depth, None, gr.bfs_opts(spin_limit=1))
+        seen = G.sync_status()
+        if seen == gr.GR_ERR_TIMEOUT:
+            break
+    assert seen == gr.GR_ERR_TIMEOUT
+    d, p = run_bfs(gr, G, 0)      # the context and the workspace are still usable
+    check(g, 0, d, p)
+
+
+def test_separate_workspaces_on_streams(gr, s16):
+    import torch
+    g, G = s16
+    srcs = [0, 7, 99, 1234]
+    wss = [gr.gr_workspace_create(G.handle, gr.GR_OP_BFS) for _ in srcs]
+    streams = [torch.cuda.Stream() for _ in srcs]
+    outs = []
+    torch.cuda.synchronize()
+    for src, ws, s in zip(srcs, wss, streams):
+        d = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        p = torch.empty_like(d)
+        gr.gr_bfs(G.handle, src, d, p, gr.bfs_opts(ws=ws, blocks_per_sm=1), stream=s)
+        outs.append((d, p))
+    torch.cuda.synchronize()
+    for src, ws, (d, p) in zip(srcs, wss, outs):
+        assert G.sync_status(ws) == 0
+        check(g, src, host(d), host(p))
+        gr.gr_workspace_destroy(ws)
+
+
+@pytest.mark.slow
+def test_config_s22_full_size(gr):
+    g = gg.rmat(22, 16, seed=2)
+    G = gr.Graph.from_csr(g)
+    hub = gg.max_degree_vertex(g)
+    for src in [hub] + list(gg.sources(g, 2, seed=2)):
+        d, p = run_bfs(gr, G, int(src))
+        check(g, int(src), d, p)
+    d2, p2 = run_bfs(gr, G, hub, direction=gr.GR_DIR_PUSH)
+    check(g, hub, d2, p2)
+    G.close()
+
+
+@pytest.mark.slow
+def test_config_grid4096_full_size(gr):
+    g = gg.grid(4096, 0.1, seed=3)
+    G = gr.Graph.from_csr(g)
+    d, p = run_bfs(gr, G, 0)
+    check(g, 0, d, p)
+    assert d.max() > 8000       # thousands of small-frontier levels
+    G.close()
