@@ -302,6 +302,42 @@ void gr_sssp_opts_default(gr_sssp_opts* o);
 gr_status gr_sssp(const gr_graph* g, int32_t src, uint32_t* dist, int32_t* pred,
                   const gr_sssp_opts* opts, void* stream);
 
+/* ---- BFS without allocation --------------------------------------------- */
+
+/*
+ * The paper has no counterpart for this entry point; it exists for callers
+ * that must not allocate device memory while they run a query: a callback of
+ * a custom device allocator or memory pool (allocating there would re-enter
+ * the allocator), a latency-critical thread that cannot afford the implicit
+ * synchronisation cudaMalloc may cause, or a host runtime that owns all
+ * device memory.  It runs the same persistent BFS as gr_bfs, but takes the
+ * CSR directly (no gr_graph handle, which would allocate) and keeps every
+ * scratch buffer in one statically sized __device__ array of about 9.6 MB
+ * that each GPU loading this library reserves until the process exits.  The
+ * call allocates nothing.
+ *
+ *   n, m, row_offsets, cols: a CSR as gr_graph_create_csr accepts it; it is
+ *     NOT validated here (the caller guarantees validity).  Limits:
+ *     n <= GR_STATIC_MAX_VERTICES and m <= GR_STATIC_MAX_EDGES, otherwise
+ *     GR_ERR_CAPACITY is returned and nothing runs.
+ *   flags: 0 or GR_SYMMETRIC (trusted: allows direction-optimising pull
+ *     levels; must only be passed for symmetric graphs with sorted rows).
+ *   depth, pred: outputs as in gr_bfs (pred may be NULL).
+ *   status: device int32* or NULL; receives GR_OK or the device-detected
+ *     error of this run (as gr_sync_status would report it) when the run ends.
+ * Asynchronous on `stream`.  The first call on a device looks up the scratch
+ * address (cudaGetSymbolAddress, which may load the module) and so must not
+ * be made while `stream` is being captured.  All calls share the one
+ * scratch array: every call clears its control block and status word first,
+ * and calls whose kernels overlap on the GPU race, so serialise them (for
+ * example, issue them on one stream).
+ */
+#define GR_STATIC_MAX_VERTICES (1 << 20)
+#define GR_STATIC_MAX_EDGES    (1 << 25)
+gr_status gr_bfs_static(int32_t n, int64_t m, const int32_t* row_offsets, const int32_t* cols,
+                        uint32_t flags, int32_t src, int32_t* depth, int32_t* pred,
+                        int32_t* status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

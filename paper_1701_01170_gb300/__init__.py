@@ -92,7 +92,10 @@ _SIGNATURES = {
     "gr_bfs": ([c_vp, c_i32, c_vp, c_vp, ctypes.POINTER(gr_bfs_opts), c_vp], c_i32),
     "gr_sssp_opts_default": ([ctypes.POINTER(gr_sssp_opts)], None),
     "gr_sssp": ([c_vp, c_i32, c_vp, c_vp, ctypes.POINTER(gr_sssp_opts), c_vp], c_i32),
+    "gr_bfs_static": ([c_i32, c_i64, c_vp, c_vp, c_u32, c_i32, c_vp, c_vp, c_vp, c_vp], c_i32),
 }
+GR_STATIC_MAX_VERTICES = 1 << 20
+GR_STATIC_MAX_EDGES = 1 << 25
 
 
 def library_path() -> str:
@@ -252,6 +255,19 @@ def gr_sssp(g, src, dist, pred=None, opts=None, stream=None):
     st = load().gr_sssp(c_vp(g), src, _ptr(dist), _ptr(pred),
                         ctypes.byref(opts) if opts is not None else None, _stream(stream))
     _check(st, "gr_sssp")
+
+
+def gr_bfs_static(n, m, row_offsets, cols, src, depth, pred=None, status=None, flags=0,
+                  stream=None):
+    """BFS that allocates nothing: scratch lives in the library's static device array.
+
+    For callers that may not allocate device memory at call time (allocator
+    callbacks, latency-critical threads, runtimes owning all device memory).
+    Calls share that array, so they must not overlap on the GPU.
+    """
+    st = load().gr_bfs_static(n, m, _ptr(row_offsets), _ptr(cols), flags, src, _ptr(depth),
+                              _ptr(pred), _ptr(status), _stream(stream))
+    _check(st, "gr_bfs_static")
 
 
 # ---- convenience: a graph resident in device memory ------------------------

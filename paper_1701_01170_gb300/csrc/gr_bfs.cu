@@ -21,6 +21,7 @@
 // m_f > m_u * do_a, pull -> push when m_f < m_u * do_b) with m_f and m_u
 // counted exactly: every discovered vertex adds its degree to m_f.
 #include <climits>
+#include <mutex>
 
 #include "gr_internal.cuh"
 
@@ -298,6 +299,156 @@ extern "C" gr_status gr_bfs(const gr_graph* g, int32_t src, int32_t* depth, int3
   void* args[] = {&a};
   if (cudaLaunchCooperativeKernel((const void*)bfs_persistent, dim3(blocks), dim3(NT), args, 0,
                                   s) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return GR_ERR_CUDA;
+  }
+  return GR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// gr_bfs_static: the BFS above, with its scratch in a fixed static area.
+//
+// Who needs this: code that must not call cudaMalloc when it runs a query —
+// a callback of a custom device allocator or memory pool (allocating there
+// would re-enter the allocator), a latency-critical thread that cannot take
+// the device-wide synchronisation cudaMalloc may imply, or a host runtime
+// that owns all device memory and forbids allocations by libraries.  For
+// them the scratch (frontier queues, edge-chunk lists, bitmaps, the control
+// block and the status word) lives in one file-scope __device__ array that
+// the CUDA module reserves on every GPU that loads this library and keeps
+// until the process exits.  The caller still provides the CSR and the
+// output arrays.
+//
+// In host code the array's name only denotes a host-side shadow symbol, so
+// the device address is fetched with cudaGetSymbolAddress, once per device,
+// by the first call on that device (with that device current).  That first
+// call may load the module, so it must not happen during stream capture.
+// All calls share the one array: each call clears the control block and the
+// status word before its launch, and two calls whose kernels overlap on the
+// GPU would race on the same scratch, so calls must be serialised (for
+// example by issuing them on one stream).
+namespace {
+
+constexpr int64_t kStaticMaxVertices = GR_STATIC_MAX_VERTICES;
+constexpr int64_t kStaticMaxEdges = GR_STATIC_MAX_EDGES;
+constexpr int kStaticBig = GR_DEFAULT_BIG_DEGREE;
+// chunks of one frontier: at most m / chunk + m / kStaticBig + 1 entries
+constexpr int64_t kStaticChunkCap =
+    kStaticMaxEdges / GR_CHUNK_EDGES + kStaticMaxEdges / kStaticBig + 2;
+constexpr int64_t kStaticWords = (kStaticMaxVertices + 31) / 32 + 1;
+
+constexpr size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t kOffCtl = 0;
+constexpr size_t kOffStatus = round256(sizeof(GrCtl));
+constexpr size_t kOffQ0 = kOffStatus + 256;  // [0, kOffQ0) is cleared on every call
+constexpr size_t kQueueBytes = round256((size_t)(kStaticMaxVertices + 1) * sizeof(int32_t));
+constexpr size_t kOffQ1 = kOffQ0 + kQueueBytes;
+constexpr size_t kChunkBytes = round256((size_t)kStaticChunkCap * sizeof(int2));
+constexpr size_t kOffCh0 = kOffQ1 + kQueueBytes;
+constexpr size_t kOffCh1 = kOffCh0 + kChunkBytes;
+constexpr size_t kBitmapBytes = round256((size_t)kStaticWords * sizeof(uint32_t));
+constexpr size_t kOffVisited = kOffCh1 + kChunkBytes;
+constexpr size_t kOffFront = kOffVisited + kBitmapBytes;
+constexpr size_t kStaticBytes = kOffFront + 3 * kBitmapBytes;  // about 9.6 MB
+
+static __device__ __align__(256) unsigned char g_bfs_static_scratch[kStaticBytes];
+
+struct StaticDevice {
+  bool ready;
+  unsigned char* base;  // device address of g_bfs_static_scratch
+  int blocks;           // co-resident grid size for bfs_persistent
+};
+constexpr int kMaxDevices = 64;
+StaticDevice g_static_dev[kMaxDevices];
+std::mutex g_static_mu;
+
+gr_status static_setup(int device, StaticDevice** out) {
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  StaticDevice& d = g_static_dev[device];
+  if (!d.ready) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_bfs_static_scratch) != cudaSuccess || !p) {
+      (void)cudaGetLastError();
+      return GR_ERR_CUDA;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return GR_ERR_CUDA;
+    }
+    const int blocks = gr_launch_blocks((const void*)bfs_persistent, NT, 0, sms, 0);
+    if (blocks <= 0) return GR_ERR_CUDA;
+    d.base = (unsigned char*)p;
+    d.blocks = blocks;
+    d.ready = true;
+  }
+  *out = &d;
+  return GR_OK;
+}
+
+}  // namespace
+
+extern "C" gr_status gr_bfs_static(int32_t n, int64_t m, const int32_t* row_offsets,
+                                   const int32_t* cols, uint32_t flags, int32_t src,
+                                   int32_t* depth, int32_t* pred, int32_t* status,
+                                   void* stream) {
+  if (n <= 0 || m < 0 || !row_offsets || (m > 0 && !cols) || !depth || src < 0 || src >= n ||
+      (flags & ~GR_SYMMETRIC))
+    return GR_ERR_INVALID_ARG;
+  if ((int64_t)n > kStaticMaxVertices || m > kStaticMaxEdges) return GR_ERR_CAPACITY;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices) {
+    (void)cudaGetLastError();
+    return GR_ERR_CUDA;
+  }
+  StaticDevice* d = nullptr;
+  gr_status st = static_setup(device, &d);
+  if (st != GR_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char* base = d->base;
+
+  BfsArgs a = {};
+  a.n = n;
+  a.m = m;
+  a.R = row_offsets;
+  a.C = cols;
+  a.depth = depth;
+  a.pred = pred;
+  a.visited = (uint32_t*)(base + kOffVisited);
+  for (int i = 0; i < 3; ++i) a.front[i] = (uint32_t*)(base + kOffFront + i * kBitmapBytes);
+  a.q[0] = (int32_t*)(base + kOffQ0);
+  a.q[1] = (int32_t*)(base + kOffQ1);
+  a.ch[0] = (int2*)(base + kOffCh0);
+  a.ch[1] = (int2*)(base + kOffCh1);
+  a.chunk_cap = kStaticChunkCap;
+  a.ctl = (GrCtl*)(base + kOffCtl);
+  a.status = (int*)(base + kOffStatus);
+  a.src = src;
+  a.nwords = (int32_t)(((int64_t)n + 31) / 32);
+  a.use_do = (flags & GR_SYMMETRIC) ? 1 : 0;
+  a.force_pull = 0;
+  a.big = kStaticBig;
+  a.track_deg = 1;  // the maximum degree is unknown without a validation pass
+  a.do_a = 0.05f;
+  a.do_b = 0.05f;
+  a.spin = GR_DEFAULT_SPIN_LIMIT;
+  a.level_stats = nullptr;
+  a.max_levels = 0;
+
+  // the control block and the status word must start at zero; the rest of
+  // the scratch is initialised by the kernel itself
+  if (cudaMemsetAsync(base, 0, kOffQ0, s) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return GR_ERR_CUDA;
+  }
+  void* args[] = {&a};
+  if (cudaLaunchCooperativeKernel((const void*)bfs_persistent, dim3(d->blocks), dim3(NT), args,
+                                  0, s) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return GR_ERR_CUDA;
+  }
+  if (status && cudaMemcpyAsync(status, base + kOffStatus, sizeof(int32_t),
+                                cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
     (void)cudaGetLastError();
     return GR_ERR_CUDA;
   }
