@@ -51,6 +51,12 @@ def parse_args():
                    help="skip the timed CPU-oracle sample (for profiler runs)")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--workload", choices=["s22", "s16", "grid", "msbfs", "batch", "serve"],
+                   default="s22",
+                   help="s22 (default, the headline workload) or one of the other configurations")
+    p.add_argument("--rates", default="2000,5000,10000,20000,50000",
+                   help="serve: Poisson arrival rates (requests/s)")
+    p.add_argument("--requests", type=int, default=400, help="serve: requests per rate")
     return p.parse_args()
 
 
@@ -182,6 +188,29 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_source_offset(rank: int) -> int:
+    """Replicas start at different sources so that ranks run different queries."""
+    return rank * 7
+
+
+def aggregate_ranks(dev_ms: float, edges: int, world: int):
+    """(max timed milliseconds over ranks, total traversed edges over ranks).
+
+    Replicas only: this is the one collective, and it runs after the timed
+    region (the data path has none).
+    """
+    if world <= 1:
+        return dev_ms, float(edges)
+    import torch
+    import torch.distributed as dist
+    device = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([dev_ms, float(edges)], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(t[1])
+
+
 def emit(obj):
     print(json.dumps(obj), flush=True)
 
@@ -274,7 +303,7 @@ def run_ours(args):
         evs[2].record(stream)
 
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    k = rank * 7   # ranks start at different sources
+    k = rank_source_offset(rank)
     for _ in range(args.warmup):
         step(srcs[k % len(srcs)], evs)
         k += 1
@@ -328,15 +357,7 @@ def run_ours(args):
 
     dev_ms = sum(t_bfs) + sum(t_sssp)
     edges = e_bfs + e_sssp
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([dev_ms, float(edges)], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        dev_ms_max, edges_all = float(mx[0]), float(t[1])
-    else:
-        dev_ms_max, edges_all = dev_ms, float(edges)
+    dev_ms_max, edges_all = aggregate_ranks(dev_ms, edges, ws)
     value = edges_all / (dev_ms_max / 1e3) / 1e9
 
     # ---- e2e: host buffers through the C ABI, copies inside the timed region
@@ -421,7 +442,7 @@ def run_e2e(gr, g, srcs, args, dev, rank):
         for h, d in zip(outs_h, outs_d):
             h.copy_(d, non_blocking=True)
 
-    k = rank * 7
+    k = rank_source_offset(rank)
     one(srcs[0])
     torch.cuda.synchronize()
     ms, edges = 0.0, 0
@@ -448,9 +469,180 @@ def run_e2e(gr, g, srcs, args, dev, rank):
                     "read back every step"}
 
 
+# ------------------------------------------------ the other configurations ---
+
+def _events_ms(fn, reps, warm=2):
+    import torch
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        s.record()
+        fn()
+        e.record()
+        e.synchronize()
+        ts.append(s.elapsed_time(e))
+    return ts
+
+
+def run_other(args):
+    """Non-default workloads: one JSON line each, same keys where they apply."""
+    import torch
+
+    import graphgen as gg
+    import paper_1701_01170_gb300 as gr
+    torch.cuda.set_device(0)
+    gr.load()
+    base = {"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "int32",
+            "data": "synthetic", "vs_baseline": None, "scaling": "weak"}
+    if args.workload in ("s16", "grid"):
+        if args.workload == "s16":
+            g = gg.rmat(16, 16, 1)
+            srcs, ops = [0], ["bfs"]
+            desc = "rmat_s16_ef16_seed1: BFS from vertex 0 (int32 depth + pred)"
+        else:
+            g = gg.grid_weighted(4096, 0.1, 3)
+            srcs = [0] + [int(x) for x in gg.sources(g, 4, seed=3)]
+            ops = ["bfs", "sssp"]
+            desc = "grid 4096x4096, 10% edges deleted (seed 3), weights U[1,1000]: BFS + SSSP"
+        G = gr.Graph.from_csr(g)
+        deg = g.degrees()
+        d = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        p = torch.empty_like(d)
+        res = {}
+        for op in ops:
+            tot_ms, tot_e, levels = 0.0, 0, []
+            for src in srcs:
+                fn = (lambda: gr.gr_bfs(G.handle, src, d, p)) if op == "bfs" else \
+                    (lambda: gr.gr_sssp(G.handle, src, d, p))
+                ts = _events_ms(fn, max(1, args.steps // len(srcs)), warm=1)
+                st = gr.gr_last_run_stats(G.handle)
+                levels.append(st["levels"])
+                reached = host_reached(d, op)
+                tot_ms += statistics.mean(ts)
+                tot_e += int(deg[reached].sum())
+            res[op] = {"gteps": tot_e / (tot_ms / 1e3) / 1e9, "ms_per_query": tot_ms / len(srcs),
+                       "levels_or_steps": levels,
+                       "us_per_level": 1e3 * tot_ms / max(1, sum(levels))}
+        assert G.sync_status() == 0
+        val = sum(r["gteps"] for r in res.values()) / len(res)
+        emit({"metric": "GTEPS", "value": val, "unit": "GTEPS", **base,
+              "ms_per_step": sum(r["ms_per_query"] for r in res.values()),
+              "higher_is_better": True, "config": {"workload": desc}, "per_op": res})
+        return
+    if args.workload == "msbfs":
+        g = gg.rmat(20, 16, 1)
+        srcs = gg.sources(g, 256, seed=4)
+        G = gr.Graph.from_csr(g)
+        D = torch.empty(256 * g.n, dtype=torch.int32, device="cuda")
+        ts = _events_ms(lambda: gr.gr_bfs_multi(G.handle, srcs, D), args.steps)
+        deg = g.degrees()
+        Dh = D.view(256, g.n).cpu().numpy()
+        edges = int(sum(int(deg[row >= 0].sum()) for row in Dh))
+        d = torch.empty(g.n, dtype=torch.int32, device="cuda")
+
+        def plain():
+            for s_ in srcs:
+                gr.gr_bfs(G.handle, int(s_), d, None)
+        tp = _events_ms(plain, max(1, args.steps // 4), warm=1)
+        ms, mp = statistics.median(ts), statistics.median(tp)
+        emit({"metric": "GTEPS", "value": edges / (ms / 1e3) / 1e9, "unit": "GTEPS", **base,
+              "ms_per_step": ms, "higher_is_better": True,
+              "config": {"workload": "rmat_s20_ef16_seed1: 256-source bit-parallel BFS "
+                                     "(sources: 256 random non-isolated vertices, seed 4)"},
+              "plain_path": {"ms_256_gr_bfs": mp, "gteps": edges / (mp / 1e3) / 1e9},
+              "speedup_vs_plain": mp / ms})
+        return
+    if args.workload == "batch":
+        from graphgen import workloads as wl
+        bgs = wl.batch_graphs(64, seed=5)
+        triples = wl.batch_jobs(bgs, 512, seed=5)
+        Gs = [gr.Graph.from_csr(b.csr) for b in bgs]
+        jobs, outs = [], []
+        for gi, op, src in triples:
+            o = torch.empty(Gs[gi].n, dtype=torch.int32, device="cuda")
+            pp = torch.empty_like(o)
+            outs.append((o, pp))
+            jobs.append(gr.gr_job(g=Gs[gi].handle, op=op, src=src, out=o.data_ptr(),
+                                  pred=pp.data_ptr()))
+        from paper_1701_01170_gb300 import tune
+        best_opts, _ = tune.tune_batch(jobs, reps=2)
+        b = gr.gr_batch_create(jobs, gr.batch_opts(**best_opts))
+        ts = _events_ms(lambda: gr.gr_batch_run(b), args.steps)
+        assert gr.gr_batch_status(b)[0] == 0
+
+        def plain():
+            for (gi, op, src), (o, pp) in zip(triples, outs):
+                if op == wl.OP_BFS:
+                    gr.gr_bfs(Gs[gi].handle, src, o, pp)
+                else:
+                    gr.gr_sssp(Gs[gi].handle, src, o, pp)
+        tp = _events_ms(plain, max(1, args.steps // 4), warm=1)
+        ms, mp = statistics.median(ts), statistics.median(tp)
+        emit({"metric": "jobs/s", "value": 512 / ms * 1e3, "unit": "jobs/s", **base,
+              "ms_per_step": ms, "higher_is_better": True,
+              "config": {"workload": "512 BFS/SSSP jobs (50/50) over 64 R-MAT graphs, scale "
+                                     "U{10..18}, ef U{8..32}, weights U[1,64]; one persistent "
+                                     "launch replayed from a CUDA graph",
+                         "batch_opts": best_opts, "info": gr.gr_batch_info(b)},
+              "plain_path": {"ms": mp, "jobs_per_s": 512 / mp * 1e3},
+              "speedup_vs_plain": mp / ms})
+        gr.gr_batch_destroy(b)
+        return
+    if args.workload == "serve":
+        run_serve(args, gr, base)
+        return
+
+
+def host_reached(d, op):
+    a = d.cpu().numpy()
+    return a >= 0 if op == "bfs" else a != -1
+
+
+def run_serve(args, gr, base):
+    import numpy as np
+    import torch
+
+    from graphgen import workloads as wl
+    from paper_1701_01170_gb300 import serve
+    graphs = {name: gr.Graph.from_csr(g) for name, g in wl.serving_graphs()}
+    cands = {name: np.flatnonzero(np.diff(G.R.cpu().numpy()) > 0) for name, G in graphs.items()}
+    multi = [n for n in graphs if n.startswith("rmat")]
+    lanes = 4
+    be = serve.GpuBackend(graphs, lanes, blocks_per_sm=1)
+    be.prepare_multi(multi)
+    budget = 16 << 30
+    names = sorted(graphs)
+    results = []
+    for rate in [float(x) for x in args.rates.split(",")]:
+        def src_of(name, rng):
+            c = cands[name]
+            return c[int(rng.integers(0, len(c)))]
+        trace = serve.poisson_trace(names, rate, args.requests, 6, src_of)
+        st = serve.serve_trace(be, trace, lanes, budget, multi_names=multi)
+        trace2 = serve.poisson_trace(names, rate, args.requests, 6, src_of)
+        st2 = serve.serve_serial(be, trace2)
+        same = all(np.array_equal(a.result, b.result) for a, b in zip(
+            sorted(trace, key=lambda r: r.rid), sorted(trace2, key=lambda r: r.rid)))
+        results.append({"rate": rate, "served": st, "serial": st2, "results_identical": same})
+    be.close()
+    best = max(results, key=lambda r: r["served"]["queries_per_s"])
+    emit({"metric": "queries/s", "value": best["served"]["queries_per_s"], "unit": "queries/s",
+          **base, "ms_per_step": best["served"]["p50_ms"], "higher_is_better": True,
+          "config": {"workload": "serving: 8 resident graphs (R-MAT s18/20/22/24 ef16, grids "
+                                 "1024^2..8192^2), Poisson BFS/SSSP 50/50, random sources, "
+                                 f"{args.requests} requests per rate, {lanes} lanes, "
+                                 "16 GB budget"},
+          "per_rate": results})
+
+
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.workload != "s22":
+        run_other(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -302,6 +302,84 @@ void gr_sssp_opts_default(gr_sssp_opts* o);
 gr_status gr_sssp(const gr_graph* g, int32_t src, uint32_t* dist, int32_t* pred,
                   const gr_sssp_opts* opts, void* stream);
 
+/* ---- multi-source BFS (batched queries) --------------------------------- */
+
+typedef struct gr_msbfs_opts {
+  int32_t direction;  /* GR_DIR_AUTO, GR_DIR_PUSH or GR_DIR_PULL (pull needs a
+                         GR_SYMMETRIC graph)                                   */
+  float push_ratio;   /* AUTO: pull once the active vertices' degree sum
+                         exceeds push_ratio * m                              */
+} gr_msbfs_opts;
+
+void gr_msbfs_opts_default(gr_msbfs_opts* o);
+
+/*
+ * k independent BFS runs from srcs[0..k) (HOST array, each in [0, n)),
+ * computed together bit-parallel, 256 sources per pass: every vertex holds
+ * one bit per source (the multi-frontier traversal the paper names as future
+ * work, Sec. 8).  depth: device int32[k * n]; depth[i * n + v] is the BFS
+ * depth of v from srcs[i] (-1 if unreachable), exactly as gr_bfs would
+ * report it.  Synchronous (the level loop reads one counter per level).  The
+ * first call on a graph allocates the graph's multi-source scratch
+ * (about 100 * n bytes), kept until gr_graph_destroy.  Calls on one graph
+ * must not overlap.
+ */
+gr_status gr_bfs_multi(const gr_graph* g, const int32_t* srcs, int32_t k, int32_t* depth,
+                       const gr_msbfs_opts* opts, void* stream);
+
+/* ---- batched jobs over many graphs -------------------------------------- */
+
+/*
+ * One BFS or SSSP query of a batch.  The tuning fields choose the per-level
+ * strategy of the job (0 = library default): do_a / do_b are the push/pull
+ * switch factors of Eq. 5-6, big_degree the row length from which a row is
+ * split into edge chunks shared by the whole job, delta the near/far bucket
+ * width of SSSP (Sec. 5.1.5).
+ */
+typedef struct gr_job {
+  const gr_graph* g;
+  int32_t op;        /* GR_OP_BFS or GR_OP_SSSP                                */
+  int32_t src;       /* in [0, n)                                              */
+  void* out;         /* device int32 depth[n] (BFS) or uint32 dist[n] (SSSP)   */
+  int32_t* pred;     /* device int32[n] or NULL                                */
+  float do_a, do_b;
+  int32_t big_degree;
+  uint32_t delta;
+} gr_job;
+
+typedef struct gr_batch_opts {
+  int32_t cluster_size;    /* CTAs (on distinct SMs) that run one job together, 1..16 */
+  int32_t clusters_per_sm; /* cap on resident clusters per SM; 0 = occupancy maximum  */
+  int32_t use_graph;       /* capture the launch once in a CUDA graph and replay it   */
+  uint32_t spin_limit;     /* reserved for bounded waits; 0 = default                 */
+} gr_batch_opts;
+
+void gr_batch_opts_default(gr_batch_opts* o);
+
+typedef struct gr_batch gr_batch;
+
+/*
+ * Prepare a batch: copies the job table to the device (sorted largest job
+ * first), allocates one scratch slot per resident cluster (sized for the
+ * largest graph), and with use_graph captures the launch in a CUDA graph.
+ * Synchronous.  The graphs and output arrays must outlive the batch.  Every
+ * job produces exactly what gr_bfs / gr_sssp produce for it.
+ */
+gr_status gr_batch_create(const gr_job* jobs, int32_t njobs, const gr_batch_opts* opts,
+                          gr_batch** out);
+
+/* Run every job of the batch in one persistent launch on `stream` (async). */
+gr_status gr_batch_run(gr_batch* b, void* stream);
+
+/* Wait for `stream`; copy per-job status codes (may be NULL); return the first error. */
+gr_status gr_batch_status(gr_batch* b, int32_t* job_status, void* stream);
+
+/* Resident clusters, cluster size and scratch bytes of a batch (host call). */
+gr_status gr_batch_info(const gr_batch* b, int32_t* clusters, int32_t* cluster_size,
+                        size_t* scratch_bytes);
+
+gr_status gr_batch_destroy(gr_batch* b);
+
 /* ---- BFS without allocation --------------------------------------------- */
 
 /*

@@ -58,6 +58,20 @@ class gr_sssp_state(ctypes.Structure):
     _fields_ = [("key", c_vp), ("threshold", c_u32)]
 
 
+class gr_msbfs_opts(ctypes.Structure):
+    _fields_ = [("direction", c_i32), ("push_ratio", c_f32)]
+
+
+class gr_job(ctypes.Structure):
+    _fields_ = [("g", c_vp), ("op", c_i32), ("src", c_i32), ("out", c_vp), ("pred", c_vp),
+                ("do_a", c_f32), ("do_b", c_f32), ("big_degree", c_i32), ("delta", c_u32)]
+
+
+class gr_batch_opts(ctypes.Structure):
+    _fields_ = [("cluster_size", c_i32), ("clusters_per_sm", c_i32), ("use_graph", c_i32),
+                ("spin_limit", c_u32)]
+
+
 class gr_run_stats(ctypes.Structure):
     _fields_ = [("levels", c_i32), ("reserved", c_i32), ("edges", c_i64), ("vertices", c_i64),
                 ("updates", c_i64)]
@@ -92,6 +106,14 @@ _SIGNATURES = {
     "gr_bfs": ([c_vp, c_i32, c_vp, c_vp, ctypes.POINTER(gr_bfs_opts), c_vp], c_i32),
     "gr_sssp_opts_default": ([ctypes.POINTER(gr_sssp_opts)], None),
     "gr_sssp": ([c_vp, c_i32, c_vp, c_vp, ctypes.POINTER(gr_sssp_opts), c_vp], c_i32),
+    "gr_msbfs_opts_default": ([ctypes.POINTER(gr_msbfs_opts)], None),
+    "gr_bfs_multi": ([c_vp, c_vp, c_i32, c_vp, ctypes.POINTER(gr_msbfs_opts), c_vp], c_i32),
+    "gr_batch_opts_default": ([ctypes.POINTER(gr_batch_opts)], None),
+    "gr_batch_create": ([c_vp, c_i32, ctypes.POINTER(gr_batch_opts), ctypes.POINTER(c_vp)], c_i32),
+    "gr_batch_run": ([c_vp, c_vp], c_i32),
+    "gr_batch_status": ([c_vp, c_vp, c_vp], c_i32),
+    "gr_batch_info": ([c_vp, c_vp, c_vp, c_vp], c_i32),
+    "gr_batch_destroy": ([c_vp], c_i32),
     "gr_bfs_static": ([c_i32, c_i64, c_vp, c_vp, c_u32, c_i32, c_vp, c_vp, c_vp, c_vp], c_i32),
 }
 GR_STATIC_MAX_VERTICES = 1 << 20
@@ -255,6 +277,65 @@ def gr_sssp(g, src, dist, pred=None, opts=None, stream=None):
     st = load().gr_sssp(c_vp(g), src, _ptr(dist), _ptr(pred),
                         ctypes.byref(opts) if opts is not None else None, _stream(stream))
     _check(st, "gr_sssp")
+
+
+def msbfs_opts(**kw) -> gr_msbfs_opts:
+    o = gr_msbfs_opts()
+    load().gr_msbfs_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def gr_bfs_multi(g, srcs, depth, opts=None, stream=None):
+    """k-source bit-parallel BFS; srcs is a host int sequence, depth a CUDA int32 (k*n) tensor."""
+    import numpy as np
+    s = np.ascontiguousarray(srcs, dtype=np.int32)
+    st = load().gr_bfs_multi(c_vp(g), s.ctypes.data_as(c_vp), len(s), _ptr(depth),
+                             ctypes.byref(opts) if opts is not None else None, _stream(stream))
+    _check(st, "gr_bfs_multi")
+
+
+def batch_opts(**kw) -> gr_batch_opts:
+    o = gr_batch_opts()
+    load().gr_batch_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def gr_batch_create(jobs, opts=None):
+    """jobs: a sequence of gr_job structures.  Returns an opaque batch handle."""
+    arr = (gr_job * len(jobs))(*jobs)
+    h = c_vp()
+    _check(load().gr_batch_create(ctypes.cast(arr, c_vp), len(jobs),
+                                  ctypes.byref(opts) if opts is not None else None,
+                                  ctypes.byref(h)), "gr_batch_create")
+    return h.value
+
+
+def gr_batch_run(b, stream=None):
+    _check(load().gr_batch_run(c_vp(b), _stream(stream)), "gr_batch_run")
+
+
+def gr_batch_status(b, njobs=None, stream=None):
+    """(first error code, per-job status list or None)."""
+    import numpy as np
+    arr = None if njobs is None else np.zeros(njobs, np.int32)
+    st = load().gr_batch_status(c_vp(b), arr.ctypes.data_as(c_vp) if arr is not None else None,
+                                _stream(stream))
+    return st, (None if arr is None else arr.tolist())
+
+
+def gr_batch_info(b):
+    c, cs, sb = c_i32(), c_i32(), ctypes.c_size_t()
+    _check(load().gr_batch_info(c_vp(b), ctypes.byref(c), ctypes.byref(cs), ctypes.byref(sb)),
+           "gr_batch_info")
+    return {"clusters": c.value, "cluster_size": cs.value, "scratch_bytes": sb.value}
+
+
+def gr_batch_destroy(b):
+    _check(load().gr_batch_destroy(c_vp(b)), "gr_batch_destroy")
 
 
 def gr_bfs_static(n, m, row_offsets, cols, src, depth, pred=None, status=None, flags=0,

@@ -373,6 +373,7 @@ extern "C" gr_status gr_graph_destroy(gr_graph* g) {
   if (!g) return GR_ERR_INVALID_ARG;
   cudaDeviceSynchronize();
   ws_free(g->ws_default);
+  gr_ms_free(g->ms);
   for (void* p : g->owned)
     if (p) cudaFree(p);
   delete g;

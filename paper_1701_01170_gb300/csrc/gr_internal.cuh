@@ -28,14 +28,16 @@
 // counters are cleared by the host (cudaMemsetAsync) before every persistent
 // launch; the status word lives separately and persists until read.
 struct GrCtl {
-  unsigned bar_count;
-  unsigned bar_gen;
+  unsigned bar_count;              // grid barrier: arrivals since launch (monotonic)
+  unsigned bar_pad;
   int abort;
   int levels;                      // BFS levels / SSSP steps executed
   int qlen[3];                     // frontier queue length, slot = step % 3
   int nchunk[3];                   // edge chunks of split rows, slot = step % 3
   int nbig[3];                     // number of split rows, slot = step % 3
   int farlen[3];                   // SSSP far pile length, slot = epoch % 3
+  int work[3];                     // dynamic work counter (queue batches / pull words)
+  int workc[3];                    // dynamic work counter (edge chunks)
   unsigned farmin[3];              // SSSP smallest distance pushed to a far pile
   int ovf_pending;                 // SSSP: some relaxation sum did not fit in 32 bits
   unsigned long long mf[3];        // sum of degrees of the next frontier
@@ -63,6 +65,9 @@ struct GrCounters {
   }
 };
 
+struct GrMsState;                  // multi-source BFS scratch (gr_msbfs.cu)
+void gr_ms_free(GrMsState* ms);
+
 struct gr_graph {
   int32_t n;
   int64_t m;
@@ -77,6 +82,7 @@ struct gr_graph {
   int device;
   int num_sms;
   gr_workspace* ws_default;
+  GrMsState* ms;                   // allocated by the first gr_bfs_multi call
 };
 
 struct gr_workspace {
@@ -149,13 +155,15 @@ __device__ __forceinline__ void gr_check_deadline(GrCtl* ctl, int* status,
   }
 }
 
-// Grid-wide barrier for a cooperative (co-resident) launch.  Sense is a
-// generation counter; the last block to arrive resets the arrival count and
-// publishes the next generation with release semantics.  Waits are bounded
-// by spin_limit polls; on timeout (or when another block aborted) the
-// function records GR_ERR_TIMEOUT, raises the abort flag and returns false,
-// and every caller must then leave the kernel.
-__device__ __forceinline__ bool gr_grid_sync(GrCtl* ctl, int* status, unsigned spin_limit) {
+// Grid-wide barrier for a cooperative (co-resident) launch.  Arrival is a
+// fire-and-forget release increment of one monotonic counter (cleared by the
+// host before every launch); block b's k-th barrier completes when the
+// counter reaches k * gridDim.x.  Waits are bounded by spin_limit polls; on
+// timeout (or when another block aborted) the function records
+// GR_ERR_TIMEOUT, raises the abort flag and returns false, and every caller
+// must then leave the kernel.  `phase` is the calling block's barrier count.
+__device__ __forceinline__ bool gr_grid_sync(GrCtl* ctl, int* status, unsigned spin_limit,
+                                             unsigned& phase) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -163,20 +171,16 @@ __device__ __forceinline__ bool gr_grid_sync(GrCtl* ctl, int* status, unsigned s
     if (gr_ld_volatile(&ctl->abort)) {
       ok = 0;
     } else {
-      unsigned gen = gr_ld_acquire(&ctl->bar_gen);
-      unsigned arrived = gr_atom_add_acq_rel(&ctl->bar_count, 1u);
-      if (arrived == gridDim.x - 1) {
-        atomicExch(&ctl->bar_count, 0u);
-        gr_st_release(&ctl->bar_gen, gen + 1u);
-      } else {
-        unsigned polls = 0;
-        while (gr_ld_acquire(&ctl->bar_gen) == gen) {
-          if (++polls > spin_limit || gr_ld_volatile(&ctl->abort)) {
-            ok = 0;
-            break;
-          }
-          __nanosleep(32);
+      phase += 1u;
+      const unsigned target = phase * gridDim.x;
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ctl->bar_count) : "memory");
+      unsigned polls = 0;
+      while ((int)(gr_ld_acquire(&ctl->bar_count) - target) < 0) {
+        if (++polls > spin_limit || gr_ld_volatile(&ctl->abort)) {
+          ok = 0;
+          break;
         }
+        __nanosleep(20);
       }
       __threadfence();
     }
@@ -189,6 +193,42 @@ __device__ __forceinline__ bool gr_grid_sync(GrCtl* ctl, int* status, unsigned s
   __syncthreads();
   return s_ok != 0;
 }
+
+// Warp-uniform dynamic work grab: lane 0 takes `amount` items from *counter
+// and the start index is broadcast to the warp.
+__device__ __forceinline__ int gr_warp_grab(int* counter, int amount, int lane) {
+  int b = 0;
+  if (lane == 0) b = atomicAdd(counter, amount);
+  return __shfl_sync(GR_FULL_MASK, b, 0);
+}
+
+#define GR_PULL_WORDS 16
+
+// Thread scopes for the query bodies (gr_bfs_body / gr_sssp_body).
+// GridScope: every thread of a cooperative (co-resident) launch; the step
+// barrier is the bounded grid barrier above.
+struct GridScope {
+  GrCtl* ctl;
+  int* status;
+  unsigned spin;
+  int64_t tid, nthreads;
+  unsigned phase;
+  __device__ __forceinline__ bool sync() { return gr_grid_sync(ctl, status, spin, phase); }
+};
+
+// ClusterScope: the threads of one thread-block cluster (possibly a single
+// CTA).  The step barrier is the hardware cluster barrier with release /
+// acquire semantics; all CTAs of a cluster are co-scheduled, so it cannot
+// wait for a CTA that never runs.  A raised abort flag ends the job.
+struct ClusterScope {
+  GrCtl* ctl;
+  int64_t tid, nthreads;
+  __device__ __forceinline__ bool sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+                 ::: "memory");
+    return __ldcg(&ctl->abort) == 0;
+  }
+};
 
 // Exclusive warp scan of an int; *total gets the warp sum.
 __device__ __forceinline__ int gr_warp_excl_scan(int x, int lane, int* total) {

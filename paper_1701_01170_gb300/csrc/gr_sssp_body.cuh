@@ -1,0 +1,228 @@
+// gr_sssp_body.cuh — one SSSP query (init, near/far steps, overflow check,
+// unpack) as a device function templated on the scope of threads that run
+// it; shared by the cooperative single-query kernel (gr_sssp.cu) and the
+// batched many-graph kernel (gr_batch.cu).  See gr_sssp.cu for the method.
+#pragma once
+
+#include <climits>
+
+#include "gr_internal.cuh"
+
+struct SsspArgs {
+  int32_t n;
+  const int32_t* __restrict__ R;
+  const int32_t* __restrict__ C;
+  const uint32_t* __restrict__ W;
+  unsigned long long* key;
+  uint32_t* dist;
+  int32_t* pred;
+  int32_t* q[2];
+  int2* ch[2];
+  int64_t chunk_cap;
+  int32_t* far[2];
+  int32_t* stamp_near;
+  int32_t* stamp_far;
+  GrCtl* ctl;
+  int* status;
+  int32_t src;
+  uint32_t delta;
+  int big;
+  int track_deg;
+  unsigned spin;
+};
+
+constexpr unsigned long long GR_KEY_INF = ~0ull;
+
+template <class S>
+__device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gtid = sc.tid;
+  const int64_t gthreads = sc.nthreads;
+  const int64_t gwarp = gtid >> 5, nwarps = gthreads >> 5;
+  GrCtl* ctl = a.ctl;
+
+  // ---- Set_Problem_Data (Alg. 1): labels infinite, preds -1, root 0 -----
+  for (int64_t v = gtid; v < a.n; v += gthreads) {
+    a.key[v] = v == a.src ? 0xffffffffull : GR_KEY_INF;
+    a.stamp_near[v] = v == a.src ? 0 : -1;
+    a.stamp_far[v] = -1;
+  }
+  if (gtid == 0) {
+    const int beg = a.R[a.src], deg = a.R[a.src + 1] - beg;
+    if (a.track_deg && deg >= a.big)
+      gr_register_chunks(a.ch[0], a.chunk_cap, &ctl->nchunk[0], &ctl->nbig[0], a.src, beg, deg,
+                         a.status);
+    else {
+      a.q[0][0] = a.src;
+      ctl->qlen[0] = 1;
+    }
+    for (int k = 0; k < 3; ++k) ctl->farmin[k] = UINT_MAX;
+  }
+  if (!sc.sync()) return;
+
+  const unsigned long long deadline = gr_globaltimer() + GR_TIME_LIMIT_NS;
+  unsigned long long T = a.delta;  // near iff dist < T
+  int fe = 0;                      // far-pile epoch
+  int it = 0;                      // near step
+  GrCounters cnt;
+  bool ovf_seen = false;
+  // step counters are read once per CTA and broadcast through shared memory
+  __shared__ int s_nq, s_nch, s_flen;
+  __shared__ unsigned s_fm;
+  for (;; ++it) {
+    const int s0 = it % 3, s1 = (it + 1) % 3, s2 = (it + 2) % 3;
+    const int fs = fe % 3;
+    if (threadIdx.x == 0) {
+      s_nq = __ldcg(&ctl->qlen[s0]);
+      s_nch = __ldcg(&ctl->nchunk[s0]);
+      s_flen = __ldcg(&ctl->farlen[fs]);
+      s_fm = __ldcg(&ctl->farmin[fs]);
+    }
+    __syncthreads();
+    const int nq = min(s_nq, a.n);
+    const int nch = (int)min((int64_t)s_nch, a.chunk_cap);
+    const int flen = min(s_flen, a.n);
+    const unsigned fm_step = s_fm;
+    if (nq + nch == 0 && flen == 0) break;
+    if (gtid == 0) {
+      gr_check_deadline(ctl, a.status, deadline);
+      ctl->qlen[s2] = 0;
+      ctl->nchunk[s2] = 0;
+      ctl->nbig[s2] = 0;
+      ctl->work[s2] = 0;
+      ctl->workc[s2] = 0;
+    }
+    int32_t* qn = a.q[(it + 1) & 1];
+    int2* chn = a.ch[(it + 1) & 1];
+    const int next_stamp = it + 1;
+
+    // join the next near frontier (once per step) — all lanes call this
+    auto to_near = [&](bool take, int32_t v) {
+      if (take) take = atomicExch(&a.stamp_near[v], next_stamp) != next_stamp;
+      int vbeg = 0, vdeg = 0;
+      if (take && a.track_deg) {
+        vbeg = __ldg(a.R + v);
+        vdeg = __ldg(a.R + v + 1) - vbeg;
+      }
+      const bool big = take && vdeg >= a.big;
+      gr_warp_append(qn, &ctl->qlen[s1], a.n, take && !big, v, lane);
+      if (big)
+        gr_register_chunks(chn, a.chunk_cap, &ctl->nchunk[s1], &ctl->nbig[s1], v, vbeg, vdeg,
+                           a.status);
+    };
+    // join far pile `epoch` (once per epoch) — all lanes call this
+    auto to_far = [&](bool take, int32_t v, unsigned d, int epoch) {
+      if (take) take = atomicExch(&a.stamp_far[v], epoch) != epoch;
+      gr_warp_append(a.far[epoch & 1], &ctl->farlen[epoch % 3], a.n, take, v, lane);
+      const unsigned mn = gr_warp_min_u32(take ? d : UINT_MAX);
+      if (lane == 0 && mn != UINT_MAX) atomicMin(&ctl->farmin[epoch % 3], mn);
+    };
+
+    if (nq + nch > 0) {
+      // ---- RELAX: advance + Update_Label / Set_Pred + Remove_Redundant ----
+      const int32_t* q = a.q[it & 1];
+      const int2* ch = a.ch[it & 1];
+      auto relax = [&](bool active, int32_t u, uint32_t du, int e, int32_t v) {
+        bool imp = false;
+        unsigned long long nd = 0;
+        if (active) {
+          ++cnt.edges;
+          nd = (unsigned long long)du + __ldg(a.W + e);
+          if (nd >= (unsigned long long)GR_INF_DIST) {
+            // not representable: drop the candidate; whether a true distance
+            // overflows is decided after convergence
+            if (!ovf_seen) {
+              ovf_seen = true;
+              atomicExch(&ctl->ovf_pending, 1);
+            }
+          } else {
+            const unsigned long long cand = (nd << 32) | (unsigned)u;
+            if (cand < a.key[v]) imp = (atomicMin(&a.key[v], cand) >> 32) > nd;
+            cnt.updates += imp;
+          }
+        }
+        to_near(imp && nd < T, v);
+        to_far(imp && nd >= T, v, (unsigned)nd, fe);
+      };
+      // warps take 32 near-frontier rows at a time: the first batch by warp
+      // index, further batches from a counter (idle warps never touch it)
+      for (int base = (int)gwarp * 32; base < nq;
+           base = (int)nwarps * 32 + gr_warp_grab(&ctl->work[s0], 32, lane)) {
+        const int i = base + lane;
+        const bool valid = i < nq;
+        int32_t u = 0;
+        int beg = 0, deg = 0;
+        uint32_t du = 0;
+        if (valid) {
+          ++cnt.verts;
+          u = __ldcg(q + i);
+          beg = __ldg(a.R + u);
+          deg = __ldg(a.R + u + 1) - beg;
+          du = (uint32_t)(a.key[u] >> 32);
+        }
+        gr_warp_expand(a.R, a.C, valid, u, beg, deg, du, lane, relax);
+      }
+      // then one 1024-edge chunk of a long row at a time
+      for (int c = (int)gwarp; c < nch; c = (int)nwarps + gr_warp_grab(&ctl->workc[s0], 1, lane)) {
+        const int2 cu = __ldcg(ch + c);
+        const int e1 = min(cu.y + GR_CHUNK_EDGES, __ldg(a.R + cu.x + 1));
+        const uint32_t du = (uint32_t)(a.key[cu.x] >> 32);
+        if (lane == 0) ++cnt.verts;
+        gr_warp_chunk(a.C, cu.x, cu.y, e1, du, lane, relax);
+      }
+    } else {
+      // ---- SPLIT: raise the threshold, move far entries below it to near --
+      const unsigned fm = fm_step;
+      unsigned long long Tn = T + a.delta;
+      if (fm != UINT_MAX) {
+        const unsigned long long jump = ((unsigned long long)fm / a.delta + 1ull) * a.delta;
+        if (jump > Tn) Tn = jump;
+      }
+      if (gtid == 0) {
+        ctl->farlen[(fe + 2) % 3] = 0;
+        ctl->farmin[(fe + 2) % 3] = UINT_MAX;
+      }
+      const int32_t* fp = a.far[fe & 1];
+      // warps take 32 far entries at a time
+      for (int base = (int)gwarp * 32; base < flen;
+           base = (int)nwarps * 32 + gr_warp_grab(&ctl->work[s0], 32, lane)) {
+        const int i = base + lane;
+        int32_t v = 0;
+        unsigned long long d = 0;
+        const bool valid = i < flen;
+        if (valid) {
+          ++cnt.verts;
+          v = __ldcg(fp + i);
+          d = a.key[v] >> 32;
+        }
+        to_near(valid && d >= T && d < Tn, v);
+        to_far(valid && d >= Tn, v, (unsigned)d, fe + 1);
+      }
+      T = Tn;
+      ++fe;
+    }
+    if (!sc.sync()) return;
+  }
+  // ---- overflow check: with every unrepresentable candidate dropped, a
+  // vertex keeps an infinite label while a reached neighbour exists only if
+  // its true distance is >= UINT32_MAX.
+  if (__ldcg(&ctl->ovf_pending)) {
+    for (int64_t u = gtid; u < a.n; u += gthreads) {
+      if ((a.key[u] >> 32) == GR_INF_DIST) continue;
+      for (int e = __ldg(a.R + u); e < __ldg(a.R + u + 1); ++e)
+        if (a.key[__ldg(a.C + e)] == GR_KEY_INF) {
+          gr_set_status(a.status, GR_ERR_OVERFLOW);
+          break;
+        }
+    }
+  }
+  // ---- unpack labels and predecessors -----------------------------------
+  for (int64_t v = gtid; v < a.n; v += gthreads) {
+    const unsigned long long k = a.key[v];
+    a.dist[v] = (uint32_t)(k >> 32);
+    if (a.pred) a.pred[v] = (int32_t)(uint32_t)(k & 0xffffffffull);
+  }
+  cnt.flush(ctl);
+  if (gtid == 0) ctl->levels = it;
+}
+
