@@ -265,6 +265,30 @@ def algorithmic_bytes(kind, st, n):
     return 8 * st["edges"] + 16 * st["vertices"] + 12 * st["updates"] + 32 * n
 
 
+def profiled_traffic() -> dict:
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the hub-source
+    launches, from the committed ncu summaries under profiles/, for the kernel versions they
+    were captured on; None for a kernel whose sources changed since (digest mismatch)."""
+    from paper_1701_01170_gb300 import _build
+    cur = _build.source_digest()
+    out = {}
+    for kind in ("bfs", "sssp"):
+        path = os.path.join(ROOT, "profiles", f"{kind}_persistent_rmat_s22.md")
+        out[kind] = None
+        try:
+            fields = {}
+            with open(path) as f:
+                for line in f:
+                    if line.startswith("- ") and ":" in line:
+                        k, v = line[2:].split(":", 1)
+                        fields[k.strip()] = v.strip().strip("`")
+            if fields.get("source_digest") == cur:
+                out[kind] = int(fields["traffic_bytes_per_launch"])
+        except (OSError, KeyError, ValueError):
+            pass
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -380,11 +404,12 @@ def run_ours(args):
     bfs_b = algorithmic_bytes("bfs", bst, n)
     sssp_b = algorithmic_bytes("sssp", sst, n)
     dominant = "sssp" if sum(t_sssp) >= sum(t_bfs) else "bfs"
+    traffic = profiled_traffic()
     roof = {}
     for kind, b, ms, stt in (("sssp", sssp_b, sssp_ms, sst), ("bfs", bfs_b, bfs_ms, bst)):
         ach = b / (ms / 1e3) / 1e9
         roof[kind] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                      "frac": ach / hbm, "traffic": None, "peak_kind": peak_note,
+                      "frac": ach / hbm, "traffic": traffic.get(kind), "peak_kind": peak_note,
                       "kernel": f"{kind}_persistent", "launch": "hub source",
                       "algorithmic_bytes": b, "launch_ms": ms, "counters": stt}
 

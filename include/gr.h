@@ -78,8 +78,9 @@ typedef struct gr_workspace gr_workspace;
  *   weights: device uint32[m] or NULL (needed only by SSSP).
  * Validates on the device and is synchronous on `stream`: returns
  * GR_ERR_INVALID_GRAPH if R[0] != 0, R[n] != m, R decreases, a column is
- * outside [0, n), a weight is 0, or (with GR_SYMMETRIC) some row is unsorted
- * or some edge has no reverse edge of equal weight.
+ * outside [0, n), a weight is 0, or (with GR_SYMMETRIC) some row is not
+ * strictly increasing or the edge multiset differs from its reverse (edges
+ * compared with their weights through two independent 64-bit hash sums).
  * On success *out owns a default workspace for BFS and SSSP.
  */
 gr_status gr_graph_create_csr(int32_t n, int64_t m, const int32_t* row_offsets,
@@ -261,8 +262,9 @@ typedef struct gr_bfs_opts {
   int32_t blocks_per_sm; /* persistent grid = blocks_per_sm * SMs; 0 = max    */
   uint32_t spin_limit;   /* grid-barrier wait budget in polls; 0 = default    */
   gr_workspace* ws;      /* NULL = the graph's default workspace              */
-  int32_t* level_stats;  /* optional device int32[3*max_levels]: per level
-                            (frontier size, direction, edges checked)        */
+  int32_t* level_stats;  /* optional device int32[4*max_levels]: per level
+                            (frontier size, 1 if pull, sum of the frontier's
+                            degrees m_f, start time in ns after level 0)   */
   int32_t max_levels;    /* capacity of level_stats in levels                 */
 } gr_bfs_opts;
 
@@ -348,7 +350,8 @@ typedef struct gr_job {
 } gr_job;
 
 typedef struct gr_batch_opts {
-  int32_t cluster_size;    /* CTAs (on distinct SMs) that run one job together, 1..16 */
+  int32_t cluster_size;    /* CTAs (on distinct SMs) that run one job together, 1..16;
+                              default 8                                              */
   int32_t clusters_per_sm; /* cap on resident clusters per SM; 0 = occupancy maximum  */
   int32_t use_graph;       /* capture the launch once in a CUDA graph and replay it   */
   uint32_t spin_limit;     /* reserved for bounded waits; 0 = default                 */
@@ -390,7 +393,7 @@ gr_status gr_batch_destroy(gr_batch* b);
  * synchronisation cudaMalloc may cause, or a host runtime that owns all
  * device memory.  It runs the same persistent BFS as gr_bfs, but takes the
  * CSR directly (no gr_graph handle, which would allocate) and keeps every
- * scratch buffer in one statically sized __device__ array of about 9.6 MB
+ * scratch buffer in one statically sized __device__ array of about 11 MB
  * that each GPU loading this library reserves until the process exits.  The
  * call allocates nothing.
  *

@@ -129,7 +129,7 @@ def load(build_if_missing: bool = False):
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    path = os.environ.get("GR_LIBRARY", _build.LIB)   # an alternative build of libgr.so
     if not os.path.exists(path):
         if not build_if_missing:
             raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build()")
@@ -254,7 +254,10 @@ def gr_filter(g, inp, in_len, out, out_len, mode=GR_FILTER_EXACT_UNIQUE, state=N
 def bfs_opts(**kw) -> gr_bfs_opts:
     o = gr_bfs_opts()
     load().gr_bfs_opts_default(ctypes.byref(o))
+    names = {f[0] for f in gr_bfs_opts._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"gr_bfs_opts has no field {k!r}")
         setattr(o, k, v)
     return o
 
@@ -262,7 +265,10 @@ def bfs_opts(**kw) -> gr_bfs_opts:
 def sssp_opts(**kw) -> gr_sssp_opts:
     o = gr_sssp_opts()
     load().gr_sssp_opts_default(ctypes.byref(o))
+    names = {f[0] for f in gr_sssp_opts._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"gr_sssp_opts has no field {k!r}")
         setattr(o, k, v)
     return o
 

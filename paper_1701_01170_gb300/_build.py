@@ -34,6 +34,20 @@ def sources() -> list[str]:
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
+def source_digest() -> str:
+    """Content hash of the CUDA sources and the C ABI header (identifies a kernel version)."""
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(f for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh")))
+    for f in files:
+        h.update(f.encode())
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    with open(os.path.join(INCLUDE, "gr.h"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def _stale(out: str, deps: list[str]) -> bool:
     if not os.path.exists(out):
         return True
@@ -41,19 +55,26 @@ def _stale(out: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile csrc/*.cu and link libgr.so; returns the library path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, defines: tuple = (),
+          out_dir: str | None = None) -> str:
+    """Compile csrc/*.cu and link libgr.so; returns the library path.
+
+    `defines` (e.g. ("GR_STREAM_COLUMNS=1",)) and `out_dir` build a variant of
+    the library elsewhere, for A/B measurements of the build-time switches.
+    """
+    bdir = out_dir or BUILD
+    lib = os.path.join(bdir, "libgr.so")
+    os.makedirs(bdir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     headers.append(os.path.join(INCLUDE, "gr.h"))
     cc = nvcc()
     jobs = []
     objs = []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
-            jobs.append([cc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj])
+            jobs.append([cc, *ARCH, *NVCC_FLAGS, *["-D" + d for d in defines], "-c", src, "-o", obj])
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))
@@ -63,11 +84,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 print(r.stdout + r.stderr)
             if r.returncode:
                 raise RuntimeError(f"nvcc failed for {cmd[-3]}")
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".{os.getpid()}.tmp"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".{os.getpid()}.tmp"
         subprocess.check_call([cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -48,6 +48,7 @@ struct ValidateOut {
   int nonisolated;
   int pad;
   unsigned long long weight_sum;
+  unsigned long long fp[4];  // symmetry fingerprints: forward / backward, two hashes
 };
 
 // Violation codes (diagnostic only; the API reports GR_ERR_INVALID_GRAPH).
@@ -80,39 +81,57 @@ __global__ void gr_validate_rows(int32_t n, int64_t m, const int32_t* __restrict
 }
 
 // Column range, weights, sortedness and (optionally) symmetry, one warp per
-// row so that the reverse-edge binary searches stay warp-local.
+// row with the lanes striding its edges (coalesced).  Symmetry is checked as
+// multiset equality {(u, v, w)} == {(v, u, w)}: every edge adds a mixed hash
+// of (u, v, w) to one pair of 64-bit sums and of (v, u, w) to another; the
+// host compares the sums.  With strictly sorted rows (checked exactly) the
+// multisets are sets, and an asymmetric graph passes only through a
+// simultaneous collision of two independent 64-bit hash sums.
+__device__ __forceinline__ unsigned long long gr_mix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
 __global__ void gr_validate_edges(int32_t n, const int32_t* __restrict__ R,
                                   const int32_t* __restrict__ C, const uint32_t* __restrict__ W,
                                   int symmetric, ValidateOut* out) {
   int lane = threadIdx.x & 31;
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  unsigned long long wsum = 0;
+  unsigned long long wsum = 0, f[4] = {0, 0, 0, 0};
   for (int64_t u = warp; u < n; u += nwarps) {
     int a = R[u], b = R[u + 1];
     if (b < a) continue;  // reported by gr_validate_rows
     for (int e = a + lane; e < b; e += 32) {
       int v = C[e];
       if (v < 0 || v >= n) { atomicCAS(&out->bad, 0, V_COL); continue; }
+      unsigned w = 0;
       if (W) {
-        if (W[e] == 0) atomicCAS(&out->bad, 0, V_WEIGHT);
-        wsum += W[e];
+        w = W[e];
+        if (w == 0) atomicCAS(&out->bad, 0, V_WEIGHT);
+        wsum += w;
       }
       if (!symmetric) continue;
-      if (e > a && C[e - 1] >= v) { atomicCAS(&out->bad, 0, V_UNSORTED); continue; }
-      // reverse edge (v, u) with the same weight
-      int lo = R[v], hi = R[v + 1] - 1, hit = -1;
-      while (lo <= hi) {
-        int mid = lo + ((hi - lo) >> 1);
-        int c = C[mid];
-        if (c == (int)u) { hit = mid; break; }
-        if (c < (int)u) lo = mid + 1; else hi = mid - 1;
-      }
-      if (hit < 0 || (W && W[hit] != W[e])) atomicCAS(&out->bad, 0, V_ASYM);
+      if (e > a && C[e - 1] >= v) atomicCAS(&out->bad, 0, V_UNSORTED);
+      const unsigned long long fw = ((unsigned long long)u << 32) | (unsigned)v;
+      const unsigned long long bw = ((unsigned long long)v << 32) | (unsigned long long)u;
+      const unsigned long long salt = (unsigned long long)w * 0xD6E8FEB86659FD93ull;
+      f[0] += gr_mix64(fw ^ salt);
+      f[1] += gr_mix64(bw ^ salt);
+      f[2] += gr_mix64(gr_mix64(fw) + salt);
+      f[3] += gr_mix64(gr_mix64(bw) + salt);
     }
   }
   wsum = gr_warp_sum_u64(wsum);
   if (lane == 0 && wsum) atomicAdd(&out->weight_sum, wsum);
+  if (symmetric) {
+    for (int k = 0; k < 4; ++k) {
+      unsigned long long x = gr_warp_sum_u64(f[k]);
+      if (lane == 0 && x) atomicAdd(&out->fp[k], x);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -130,7 +149,7 @@ static int64_t chunk_capacity(const gr_graph* g, int big) {
 static size_t ws_bytes(const gr_graph* g, int32_t ops) {
   size_t n = (size_t)g->n + 1, bw = bitmap_words(g->n);
   size_t b = sizeof(GrCtl) + 2 * sizeof(int);
-  b += 2 * n * sizeof(int32_t);                                  // queues
+  b += 4 * n * sizeof(int32_t);                                  // queues, unvisited lists
   b += 2 * (size_t)chunk_capacity(g, 32) * sizeof(int2);         // chunks (smallest big)
   b += 4 * bw * sizeof(uint32_t);                                // visited + 3 frontiers
   b += n * sizeof(int32_t) + bw * sizeof(uint32_t);              // filter scratch
@@ -143,7 +162,8 @@ static size_t ws_bytes(const gr_graph* g, int32_t ops) {
 
 static void ws_free(gr_workspace* ws) {
   if (!ws) return;
-  void* ptrs[] = {ws->ctl, ws->status, ws->q[0], ws->q[1], ws->chunks[0], ws->chunks[1],
+  void* ptrs[] = {ws->ctl, ws->status, ws->q[0], ws->q[1], ws->ulist[0], ws->ulist[1],
+                  ws->chunks[0], ws->chunks[1],
                   ws->visited, ws->front[0], ws->front[1], ws->front[2], ws->key,
                   ws->far[0], ws->far[1], ws->stamp_near, ws->stamp_far, ws->first_idx,
                   ws->claim, ws->block_sums, ws->tags, ws->item_off, ws->dev_len};
@@ -178,6 +198,8 @@ static gr_status ws_create(const gr_graph* g, int32_t ops, gr_workspace** out) {
   ALLOC(ws->status, sizeof(int));
   ALLOC(ws->q[0], n * sizeof(int32_t));
   ALLOC(ws->q[1], n * sizeof(int32_t));
+  ALLOC(ws->ulist[0], n * sizeof(int32_t));
+  ALLOC(ws->ulist[1], n * sizeof(int32_t));
   ALLOC(ws->chunks[0], ws->chunk_cap * sizeof(int2));
   ALLOC(ws->chunks[1], ws->chunk_cap * sizeof(int2));
   ALLOC(ws->visited, bw * sizeof(uint32_t));
@@ -357,6 +379,9 @@ extern "C" gr_status gr_graph_create_csr(int32_t n, int64_t m, const int32_t* ro
     (void)cudaGetLastError();
     return fail(GR_ERR_CUDA);
   }
+  if (h_out.bad == 0 && (flags & GR_SYMMETRIC) &&
+      (h_out.fp[0] != h_out.fp[1] || h_out.fp[2] != h_out.fp[3]))
+    h_out.bad = V_ASYM;
   if (h_out.bad != 0) return fail(GR_ERR_INVALID_GRAPH);
   g->max_degree = h_out.max_degree;
   g->nonisolated = h_out.nonisolated;

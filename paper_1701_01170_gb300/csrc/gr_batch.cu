@@ -54,7 +54,8 @@ struct BatchArgs {
 
 // slot layout (byte offsets, 256-aligned)
 struct SlotLayout {
-  size_t ctl, job, q0, q1, ch0, ch1, vis, fr0, fr1, fr2, key, far0, far1, stn, stf, total;
+  size_t ctl, job, q0, q1, ul0, ul1, ch0, ch1, vis, fr0, fr1, fr2, key, far0, far1, stn, stf,
+      total;
 };
 
 size_t r256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -70,6 +71,8 @@ SlotLayout slot_layout(int32_t nmax, int64_t chunk_cap) {
   L.job = o; o += 256;
   L.q0 = o; o += nq;
   L.q1 = o; o += nq;
+  L.ul0 = o; o += nq;
+  L.ul1 = o; o += nq;
   L.ch0 = o; o += nc;
   L.ch1 = o; o += nc;
   L.vis = o; o += nb;
@@ -106,6 +109,7 @@ __global__ void __launch_bounds__(BT) batch_kernel(BatchArgs b, SlotLayout L) {
   const unsigned csize = cluster_nctarank();
   const unsigned crank = cluster_ctarank();
   const unsigned slot = blockIdx.x / csize;
+  __shared__ GrArena ar;  // staging buffers, shared by the BFS and SSSP bodies
   unsigned char* base = b.scratch + (size_t)slot * b.slot_bytes;
   GrCtl* ctl = (GrCtl*)(base + L.ctl);
   int* job_cell = (int*)(base + L.job);
@@ -135,6 +139,8 @@ __global__ void __launch_bounds__(BT) batch_kernel(BatchArgs b, SlotLayout L) {
       a.front[2] = (uint32_t*)(base + L.fr2);
       a.q[0] = (int32_t*)(base + L.q0);
       a.q[1] = (int32_t*)(base + L.q1);
+      a.ulist[0] = (int32_t*)(base + L.ul0);
+      a.ulist[1] = (int32_t*)(base + L.ul1);
       a.ch[0] = (int2*)(base + L.ch0);
       a.ch[1] = (int2*)(base + L.ch1);
       a.chunk_cap = b.chunk_cap;
@@ -149,7 +155,7 @@ __global__ void __launch_bounds__(BT) batch_kernel(BatchArgs b, SlotLayout L) {
       a.do_a = J.do_a;
       a.do_b = J.do_b;
       a.spin = b.spin;
-      gr_bfs_body(a, sc);
+      gr_bfs_body(a, sc, ar);
     } else {
       SsspArgs a = {};
       a.n = J.n;
@@ -175,7 +181,7 @@ __global__ void __launch_bounds__(BT) batch_kernel(BatchArgs b, SlotLayout L) {
       a.big = J.big;
       a.track_deg = J.max_degree >= J.big;
       a.spin = b.spin;
-      gr_sssp_body(a, sc);
+      gr_sssp_body(a, sc, ar);
     }
     cluster_barrier();  // the job is complete before rank 0 reuses the slot
   }
@@ -201,11 +207,7 @@ struct gr_batch {
   cudaGraphExec_t exec;
 };
 
-static uint32_t job_delta(const gr_graph* g) {
-  if (g->m == 0 || g->nonisolated == 0) return 1;
-  double d = 32.0 * ((double)g->weight_sum / (double)g->m) / ((double)g->m / g->nonisolated);
-  return (uint32_t)std::min(std::max(d, 1.0), 1e9);
-}
+static uint32_t job_delta(const gr_graph* g) { return gr_default_delta(g); }
 
 static cudaError_t batch_enqueue(gr_batch* b, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(b->d_next, 0, sizeof(int), s);
@@ -238,7 +240,7 @@ static void batch_free(gr_batch* b) {
 
 extern "C" void gr_batch_opts_default(gr_batch_opts* o) {
   if (!o) return;
-  o->cluster_size = 1;
+  o->cluster_size = 8;
   o->clusters_per_sm = 0;
   o->use_graph = 1;
   o->spin_limit = GR_DEFAULT_SPIN_LIMIT;

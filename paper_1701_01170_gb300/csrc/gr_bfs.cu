@@ -32,7 +32,8 @@ constexpr int NT = GR_PERSIST_THREADS;
 __global__ void __launch_bounds__(NT, 3) bfs_persistent(BfsArgs a) {
   GridScope sc{a.ctl, a.status, a.spin, (int64_t)blockIdx.x * NT + threadIdx.x,
                (int64_t)gridDim.x * NT, 0u};
-  gr_bfs_body(a, sc);
+  __shared__ GrArena ar;
+  gr_bfs_body(a, sc, ar);
 }
 
 }  // namespace
@@ -76,6 +77,8 @@ extern "C" gr_status gr_bfs(const gr_graph* g, int32_t src, int32_t* depth, int3
   for (int i = 0; i < 3; ++i) a.front[i] = ws->front[i];
   a.q[0] = ws->q[0];
   a.q[1] = ws->q[1];
+  a.ulist[0] = ws->ulist[0];
+  a.ulist[1] = ws->ulist[1];
   a.ch[0] = ws->chunks[0];
   a.ch[1] = ws->chunks[1];
   a.chunk_cap = ws->chunk_cap;
@@ -150,7 +153,7 @@ constexpr size_t kOffCh1 = kOffCh0 + kChunkBytes;
 constexpr size_t kBitmapBytes = round256((size_t)kStaticWords * sizeof(uint32_t));
 constexpr size_t kOffVisited = kOffCh1 + kChunkBytes;
 constexpr size_t kOffFront = kOffVisited + kBitmapBytes;
-constexpr size_t kStaticBytes = kOffFront + 3 * kBitmapBytes;  // about 9.6 MB
+constexpr size_t kStaticBytes = kOffFront + 3 * kBitmapBytes;  // about 11 MB
 
 static __device__ __align__(256) unsigned char g_bfs_static_scratch[kStaticBytes];
 

@@ -8,6 +8,10 @@
 
 #include "gr_internal.cuh"
 
+#ifndef GR_VISIT_STRIPS
+#define GR_VISIT_STRIPS 2  // 32-edge strips a warp expands per round
+#endif
+
 struct BfsArgs {
   int32_t n;
   int64_t m;
@@ -18,6 +22,7 @@ struct BfsArgs {
   uint32_t* visited;
   uint32_t* front[3];
   int32_t* q[2];
+  int32_t* ulist[2];  // unvisited lists of pull levels (NULL: rescan the bitmap every level)
   int2* ch[2];
   int64_t chunk_cap;
   GrCtl* ctl;
@@ -39,7 +44,7 @@ struct BfsArgs {
 // S::sync() is the step barrier (a bounded grid barrier for the cooperative
 // single-query kernel, the hardware cluster barrier for batched jobs).
 template <class S>
-__device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc) {
+__device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar) {
   const int lane = threadIdx.x & 31;
   const int64_t gtid = sc.tid;
   const int64_t gthreads = sc.nthreads;
@@ -81,6 +86,13 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc) {
   // (one L2 request per CTA instead of one per warp)
   __shared__ int s_nq, s_nch, s_nbig;
   __shared__ unsigned long long s_mf;
+  __shared__ int s_qcnt, s_qbase, s_ucnt, s_ubase, s_nu;
+  GrStage stage{ar.buf0, &s_qcnt, &s_qbase};
+  GrStage ustage{ar.buf1, &s_ucnt, &s_ubase};
+  __shared__ int s_bcnt, s_btot[2];
+  GrBigStage bstage{ar.bv, ar.bb, ar.bd, ar.bo, &s_bcnt, s_btot};
+  __shared__ unsigned long long s_mfsum;
+  int list_ready = 0;  // the previous level was a pull level that wrote an unvisited list
   int pull = 0;
   int L = 0;
   for (;; ++L) {
@@ -90,6 +102,11 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc) {
       s_nch = __ldcg(&ctl->nchunk[s0]);
       s_nbig = __ldcg(&ctl->nbig[s0]);
       s_mf = __ldcg(&ctl->mf[s0]);
+      s_nu = __ldcg(&ctl->ulen[s0]);
+      stage.reset();
+      ustage.reset();
+      bstage.reset();
+      s_mfsum = 0ull;
     }
     __syncthreads();
     const int nq = min(s_nq, a.n);
@@ -108,11 +125,14 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc) {
       else if (pull && (double)mf < (double)mu * a.do_b) pull = 0;
     }
     if (gtid == 0) {
-      gr_check_deadline(ctl, a.status, deadline);
+      if ((L & 63) == 0) gr_check_deadline(ctl, a.status, deadline);
       if (a.level_stats && L < a.max_levels) {
-        a.level_stats[3 * L] = nf;
-        a.level_stats[3 * L + 1] = pull;
-        a.level_stats[3 * L + 2] = (int)min(mf, (unsigned long long)INT_MAX);
+        a.level_stats[4 * L] = nf;
+        a.level_stats[4 * L + 1] = pull;
+        a.level_stats[4 * L + 2] = (int)min(mf, (unsigned long long)INT_MAX);
+        // start of this level in ns after the first level started
+        a.level_stats[4 * L + 3] =
+            (int)min(gr_globaltimer() - (deadline - GR_TIME_LIMIT_NS), (unsigned long long)INT_MAX);
       }
       ctl->qlen[s2] = 0;
       ctl->nchunk[s2] = 0;
@@ -120,6 +140,7 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc) {
       ctl->mf[s2] = 0ull;
       ctl->work[s2] = 0;
       ctl->workc[s2] = 0;
+      ctl->ulen[s2] = 0;
     }
     if (a.use_do)
       for (int64_t w = gtid; w < a.nwords; w += gthreads) a.front[s2][w] = 0u;
@@ -129,25 +150,30 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc) {
     uint32_t* fnext = a.front[s1];
     unsigned long long my_mf = 0;
     const int next_depth = L + 1;
+    const bool list_pull = pull && list_ready;
 
     if (!pull) {
       // ---- push: advance + visit + cull fused ----------------------------
       const int32_t* q = a.q[L & 1];
       const int2* ch = a.ch[L & 1];
-      auto visit = [&](bool active, int32_t u, uint32_t, int, int32_t v) {
-        bool won = false;
-        if (active) {
-          ++cnt.edges;
-          const uint32_t bit = 1u << (v & 31);
-          uint32_t* wp = a.visited + (v >> 5);
-          if (!(*wp & bit)) won = !(atomicOr(wp, bit) & bit);
-        }
+      // a large frontier mostly meets visited vertices: test with a plain load
+      // before claiming; a small one (mesh-like graphs) claims directly and
+      // saves a dependent round trip per level
+      const bool direct_claim = nf < GR_DIRECT_CLAIM_FRONTIER;
+      // pass 2 of the multi-strip expansion: the visited word of each target
+      auto pre = [&](bool active, int, int32_t v) -> uint32_t {
+        return (active && !direct_claim) ? a.visited[v >> 5] : 0u;
+      };
+      auto visit = [&](bool active, int32_t u, uint32_t, int, int32_t v, uint32_t word) {
+        if (active) ++cnt.edges;
+        const bool try_claim = active && (direct_claim || !(word & (1u << (v & 31))));
+        const bool won = gr_warp_claim(a.visited, try_claim, v, lane);
+        if (a.use_do) gr_warp_set_bit(fnext, won, v, lane);
         int vbeg = 0, vdeg = 0;
         if (won) {
           ++cnt.updates;
           a.depth[v] = next_depth;
           if (a.pred) a.pred[v] = u;
-          if (a.use_do) atomicOr(fnext + (v >> 5), 1u << (v & 31));
           if (a.track_deg) {
             vbeg = __ldg(a.R + v);
             vdeg = __ldg(a.R + v + 1) - vbeg;
@@ -155,15 +181,15 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc) {
           }
         }
         const bool big = won && vdeg >= a.big;
-        gr_warp_append(qn, &ctl->qlen[s1], a.n, won && !big, v, lane);
+        stage.append(qn, &ctl->qlen[s1], a.n, won && !big, v, lane);
         if (big)
-          gr_register_chunks(chn, a.chunk_cap, &ctl->nchunk[s1], &ctl->nbig[s1], v, vbeg, vdeg,
-                             a.status);
+          bstage.add(chn, a.chunk_cap, &ctl->nchunk[s1], &ctl->nbig[s1], v, vbeg, vdeg,
+                     a.status);
       };
       // warps take 32 frontier rows at a time: the first batch by warp index,
       // further batches from a counter (idle warps never touch it)
       for (int base = (int)gwarp * 32; base < nq;
-           base = (int)nwarps * 32 + gr_warp_grab(&ctl->work[s0], 32, lane)) {
+           base = gr_next_batch(base, nq, (int)nwarps * 32, &ctl->work[s0], 32, lane)) {
         const int i = base + lane;
         const bool valid = i < nq;
         int32_t u = 0;
@@ -174,49 +200,61 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc) {
           beg = __ldg(a.R + u);
           deg = __ldg(a.R + u + 1) - beg;
         }
-        gr_warp_expand(a.R, a.C, valid, u, beg, deg, 0u, lane, visit);
+        gr_warp_expand_u<GR_VISIT_STRIPS>(a.R, a.C, valid, u, beg, deg, 0u, lane, pre, visit);
       }
       // then one 1024-edge chunk of a long row at a time
-      for (int c = (int)gwarp; c < nch; c = (int)nwarps + gr_warp_grab(&ctl->workc[s0], 1, lane)) {
+      for (int c = (int)gwarp; c < nch; c = gr_next_batch(c, nch, (int)nwarps, &ctl->workc[s0], 1, lane)) {
         const int2 cu = __ldcg(ch + c);
         const int e1 = min(cu.y + GR_CHUNK_EDGES, __ldg(a.R + cu.x + 1));
         if (lane == 0) ++cnt.verts;
-        gr_warp_chunk(a.C, cu.x, cu.y, e1, 0u, lane, visit);
+        gr_warp_chunk_u<GR_VISIT_STRIPS>(a.C, cu.x, cu.y, e1, 0u, lane, pre, visit);
       }
     } else {
       // ---- pull: unvisited vertices look for a parent in the frontier ----
+      // (Alg. 2 Reverse_Advance: the step yields the next active frontier and
+      // the next unvisited frontier)
       const uint32_t* fcur = a.front[s0];
-      // warps take GR_PULL_WORDS visited words (32 vertices each) at a time
-      for (int wb = (int)gwarp * GR_PULL_WORDS; wb < a.nwords;
-           wb = (int)nwarps * GR_PULL_WORDS + gr_warp_grab(&ctl->work[s0], GR_PULL_WORDS, lane)) {
-        const int we = min(wb + GR_PULL_WORDS, a.nwords);
-      for (int64_t w = wb; w < we; ++w) {
-        const uint32_t word = a.visited[w];
-        if (word == 0xffffffffu) continue;
-        const int64_t v64 = w * 32 + lane;
-        const int32_t v = (int32_t)v64;
-        const bool cand = v64 < a.n && !((word >> lane) & 1u);
+      int32_t* unext = a.ulist[0] ? a.ulist[(L + 1) & 1] : nullptr;
+      // First frontier neighbour in row order of each lane's candidate, or -1.
+      // Each lane scans its first GR_PULL_SERIAL neighbours alone (rows are
+      // sorted, so hubs come first and most candidates stop early); longer
+      // rows that still need more are then scanned by the whole warp, 32
+      // neighbours a round.  All 32 lanes call.
+      auto find_parent = [&](bool cand, int beg, int deg) -> int32_t {
         int32_t found = -1;
-        int beg = 0, deg = 0;
-        if (cand) {
-          ++cnt.verts;
-          beg = __ldg(a.R + v);
-          deg = __ldg(a.R + v + 1) - beg;
-          for (int e = beg; e < beg + deg; ++e) {
-            ++cnt.edges;
-            const int32_t u = __ldg(a.C + e);
-            if ((fcur[u >> 5] >> (u & 31)) & 1u) {
-              found = u;
+        const int p = cand ? min(deg, GR_PULL_SERIAL) : 0;
+        for (int e = beg; e < beg + p; ++e) {
+          ++cnt.edges;
+          const int32_t u = __ldg(a.C + e);
+          if ((fcur[u >> 5] >> (u & 31)) & 1u) {
+            found = u;
+            break;
+          }
+        }
+        unsigned pending = __ballot_sync(GR_FULL_MASK, cand && found < 0 && deg > GR_PULL_SERIAL);
+        while (pending) {
+          const int l = __ffs(pending) - 1;
+          pending &= pending - 1u;
+          const int lb = __shfl_sync(GR_FULL_MASK, beg, l);
+          const int le = lb + __shfl_sync(GR_FULL_MASK, deg, l);
+          int32_t f = -1;
+          for (int e0 = lb + GR_PULL_SERIAL; e0 < le; e0 += 32) {
+            const int e = e0 + lane;
+            const bool ok = e < le;
+            const int32_t u = ok ? __ldg(a.C + e) : 0;
+            if (ok) ++cnt.edges;
+            const unsigned hm = __ballot_sync(GR_FULL_MASK, ok && ((fcur[u >> 5] >> (u & 31)) & 1u));
+            if (hm) {
+              f = __shfl_sync(GR_FULL_MASK, u, __ffs(hm) - 1);
               break;
             }
           }
+          if (lane == l) found = f;
         }
-        const unsigned hit = __ballot_sync(GR_FULL_MASK, found >= 0);
-        if (hit == 0u) continue;
-        if (lane == 0) {
-          a.visited[w] = word | hit;
-          fnext[w] = hit;
-        }
+        return found;
+      };
+      // record one candidate's outcome; all 32 lanes
+      auto commit = [&](bool valid, int32_t v, int32_t found, int beg, int deg) {
         if (found >= 0) {
           ++cnt.updates;
           a.depth[v] = next_depth;
@@ -224,15 +262,75 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc) {
           my_mf += (unsigned long long)deg;
         }
         const bool big = found >= 0 && deg >= a.big;
-        gr_warp_append(qn, &ctl->qlen[s1], a.n, found >= 0 && !big, v, lane);
+        stage.append(qn, &ctl->qlen[s1], a.n, found >= 0 && !big, v, lane);
         if (big)
-          gr_register_chunks(chn, a.chunk_cap, &ctl->nchunk[s1], &ctl->nbig[s1], v, beg, deg,
-                             a.status);
-      }
+          bstage.add(chn, a.chunk_cap, &ctl->nchunk[s1], &ctl->nbig[s1], v, beg, deg,
+                     a.status);
+        // a vertex that can still be discovered stays on the unvisited list
+        if (unext) ustage.append(unext, &ctl->ulen[s1], a.n, valid && found < 0 && deg > 0, v, lane);
+      };
+      if (list_pull) {
+        // the previous level was a pull level: walk its unvisited list
+        const int32_t* cand = a.ulist[L & 1];
+        const int nc = min(s_nu, a.n);
+        for (int base = (int)gwarp * 32; base < nc;
+             base = gr_next_batch(base, nc, (int)nwarps * 32, &ctl->work[s0], 32, lane)) {
+          const int i = base + lane;
+          const bool valid = i < nc;
+          int32_t v = 0, found = -1;
+          int beg = 0, deg = 0;
+          if (valid) {
+            ++cnt.verts;
+            v = __ldcg(cand + i);
+            beg = __ldg(a.R + v);
+            deg = __ldg(a.R + v + 1) - beg;
+          }
+          found = find_parent(valid, beg, deg);
+          // list entries are distinct vertices: set their bits, one atomic per word
+          gr_warp_set_bit(a.visited, found >= 0, v, lane);
+          gr_warp_set_bit(fnext, found >= 0, v, lane);
+          commit(valid, v, found, beg, deg);
+        }
+      } else {
+        // first pull level: the unvisited set is the complement of the visited
+        // bitmap; warps take GR_PULL_WORDS words (32 vertices each) at a time
+        for (int wb = (int)gwarp * GR_PULL_WORDS; wb < a.nwords;
+             wb = gr_next_batch(wb, a.nwords, (int)nwarps * GR_PULL_WORDS, &ctl->work[s0],
+                                GR_PULL_WORDS, lane)) {
+          const int we = min(wb + GR_PULL_WORDS, a.nwords);
+          for (int64_t w = wb; w < we; ++w) {
+            const uint32_t word = a.visited[w];
+            if (word == 0xffffffffu) continue;
+            const int64_t v64 = w * 32 + lane;
+            const int32_t v = (int32_t)v64;
+            const bool cand = v64 < a.n && !((word >> lane) & 1u);
+            int32_t found = -1;
+            int beg = 0, deg = 0;
+            if (cand) {
+              ++cnt.verts;
+              beg = __ldg(a.R + v);
+              deg = __ldg(a.R + v + 1) - beg;
+            }
+            found = find_parent(cand, beg, deg);
+            // the warp owns this word: visited and next-frontier bits by ballot
+            const unsigned hit = __ballot_sync(GR_FULL_MASK, found >= 0);
+            if (hit != 0u && lane == 0) {
+              a.visited[w] = word | hit;
+              fnext[w] = hit;
+            }
+            commit(cand, v, found, beg, deg);
+          }
+        }
       }
     }
+    stage.flush(qn, &ctl->qlen[s1], a.n);
+    if (pull && a.ulist[0]) ustage.flush(a.ulist[(L + 1) & 1], &ctl->ulen[s1], a.n);
+    list_ready = pull && a.ulist[0] != nullptr;
+    bstage.flush(chn, a.chunk_cap, &ctl->nchunk[s1], &ctl->nbig[s1], a.status);
     my_mf = gr_warp_sum_u64(my_mf);
-    if (lane == 0 && my_mf) atomicAdd(&ctl->mf[s1], my_mf);
+    if (lane == 0 && my_mf) atomicAdd(&s_mfsum, my_mf);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_mfsum) atomicAdd(&ctl->mf[s1], s_mfsum);
     if (!sc.sync()) return;
   }
   cnt.flush(ctl);

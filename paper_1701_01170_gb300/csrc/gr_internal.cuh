@@ -13,9 +13,30 @@
 
 #define GR_FULL_MASK 0xffffffffu
 
+// Build-time switches (defaults are the measured best on GB300):
+// GR_CLAIM_AGGREGATE  1: warp-aggregated bitmap claims (one atomic per word)
+//                     0: one atomicOr per lane (measured 3x faster on R-MAT
+//                        push levels and on grids: match/reduce cost more
+//                        than the atomics they save)
+// GR_STREAM_COLUMNS   1: column/weight streams loaded with evict-first hints
+//                        (measured 13% faster SSSP: the streams no longer
+//                        evict the L2-resident keys)
+//                     0: plain read-only loads
+#ifndef GR_CLAIM_AGGREGATE
+#define GR_CLAIM_AGGREGATE 0
+#endif
+#ifndef GR_STREAM_COLUMNS
+#define GR_STREAM_COLUMNS 1
+#endif
+#if GR_STREAM_COLUMNS
+#define GR_LDSTREAM(p) __ldcs(p)
+#else
+#define GR_LDSTREAM(p) __ldg(p)
+#endif
+
 // Library defaults (tunable per call through gr_bfs_opts / gr_sssp_opts).
 #define GR_DEFAULT_BIG_DEGREE 1024   // rows >= this are split into edge chunks
-#define GR_CHUNK_EDGES 1024          // edges per chunk of a split row
+#define GR_CHUNK_EDGES 256           // edges per chunk of a split row
 #define GR_DEFAULT_SPIN_LIMIT (1u << 24)
 #define GR_TIME_LIMIT_NS (60ull * 1000000000ull)  // persistent kernels give up after 60 s
 #define GR_PERSIST_THREADS 512
@@ -38,6 +59,7 @@ struct GrCtl {
   int farlen[3];                   // SSSP far pile length, slot = epoch % 3
   int work[3];                     // dynamic work counter (queue batches / pull words)
   int workc[3];                    // dynamic work counter (edge chunks)
+  int ulen[3];                     // BFS unvisited-list length, slot = level % 3
   unsigned farmin[3];              // SSSP smallest distance pushed to a far pile
   int ovf_pending;                 // SSSP: some relaxation sum did not fit in 32 bits
   unsigned long long mf[3];        // sum of degrees of the next frontier
@@ -46,10 +68,13 @@ struct GrCtl {
   unsigned long long updates;      // BFS discoveries / SSSP successful relaxations
 };
 
-// Per-thread work counters of a persistent kernel, flushed once at exit.
+// Per-thread work counters of a persistent kernel, flushed once at exit:
+// warp sums, then a shared-memory sum per CTA, then one global atomic per
+// CTA and counter.  Every thread of the CTA must call flush().
 struct GrCounters {
   unsigned long long edges = 0, verts = 0, updates = 0;
   __device__ __forceinline__ void flush(GrCtl* ctl) {
+    __shared__ unsigned long long s_sum[3];
     unsigned long long e = edges, v = verts, u = updates;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -57,10 +82,18 @@ struct GrCounters {
       v += __shfl_xor_sync(0xffffffffu, v, o);
       u += __shfl_xor_sync(0xffffffffu, u, o);
     }
+    if (threadIdx.x < 3) s_sum[threadIdx.x] = 0ull;
+    __syncthreads();
     if ((threadIdx.x & 31) == 0) {
-      if (e) atomicAdd(&ctl->edges, e);
-      if (v) atomicAdd(&ctl->verts, v);
-      if (u) atomicAdd(&ctl->updates, u);
+      if (e) atomicAdd(&s_sum[0], e);
+      if (v) atomicAdd(&s_sum[1], v);
+      if (u) atomicAdd(&s_sum[2], u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (s_sum[0]) atomicAdd(&ctl->edges, s_sum[0]);
+      if (s_sum[1]) atomicAdd(&ctl->verts, s_sum[1]);
+      if (s_sum[2]) atomicAdd(&ctl->updates, s_sum[2]);
     }
   }
 };
@@ -92,6 +125,7 @@ struct gr_workspace {
   int* status;
   int* h_status;        // pinned host mirror used by gr_sync_status
   int32_t* q[2];        // frontier queues (ping-pong), n entries each
+  int32_t* ulist[2];    // BFS unvisited lists (ping-pong), n entries each
   int2* chunks[2];      // (row, first edge) chunks of split rows (ping-pong)
   int64_t chunk_cap;
   uint32_t* visited;    // n bits
@@ -202,7 +236,19 @@ __device__ __forceinline__ int gr_warp_grab(int* counter, int amount, int lane) 
   return __shfl_sync(GR_FULL_MASK, b, 0);
 }
 
-#define GR_PULL_WORDS 16
+// Next batch start of the "static first, dynamic after" work loops: the
+// first round covers [0, static_span) by warp index; when that already
+// covered `total` items the loop ends without touching the counter.
+__device__ __forceinline__ int gr_next_batch(int cur, int total, int static_span, int* counter,
+                                             int amount, int lane) {
+  (void)cur;
+  if (total <= static_span) return total;
+  return static_span + gr_warp_grab(counter, amount, lane);
+}
+
+#define GR_PULL_WORDS 4
+#define GR_PULL_SERIAL 64  // neighbours a pull candidate scans alone before the warp helps
+#define GR_DIRECT_CLAIM_FRONTIER 32768  // below this frontier size BFS claims without a pre-read
 
 // Thread scopes for the query bodies (gr_bfs_body / gr_sssp_body).
 // GridScope: every thread of a cooperative (co-resident) launch; the step
@@ -265,6 +311,82 @@ __device__ __forceinline__ void gr_warp_append(int32_t* q, int* len, int64_t cap
   }
 }
 
+// Warp-aggregated claim of vertex v in a bitmap.  Lanes whose vertices share
+// a 32-bit word (common: a hub's neighbours have dense, nearby ids) issue ONE
+// atomicOr with their combined bits instead of up to 32 atomics to one
+// address; among lanes claiming the same vertex only the lowest may win.
+// Returns true for the lane that newly set its bit.  All 32 lanes call.
+__device__ __forceinline__ bool gr_warp_claim(uint32_t* bm, bool active, int32_t v, int lane) {
+#if !GR_CLAIM_AGGREGATE
+  if (!active) return false;
+  const uint32_t b1 = 1u << (v & 31);
+  return !(atomicOr(bm + (v >> 5), b1) & b1);
+#endif
+  const unsigned wkey = active ? (unsigned)v >> 5 : (0x80000000u | (unsigned)lane);
+  const unsigned vkey = active ? (unsigned)v : (0x80000000u | (unsigned)lane);
+  const unsigned peers = __match_any_sync(GR_FULL_MASK, wkey);
+  const unsigned same = __match_any_sync(GR_FULL_MASK, vkey);
+  const uint32_t bit = active ? 1u << (v & 31) : 0u;
+  const uint32_t bits = __reduce_or_sync(peers, bit);
+  const int leader = __ffs(peers) - 1;
+  uint32_t old = 0u;
+  if (active && lane == leader) old = atomicOr(bm + (v >> 5), bits);
+  old = __shfl_sync(GR_FULL_MASK, old, leader);
+  return active && !(old & bit) && (__ffs(same) - 1) == lane;
+}
+
+// Warp-aggregated setting of bit v in a bitmap (no result needed): one
+// atomicOr per distinct word.  All 32 lanes call.
+__device__ __forceinline__ void gr_warp_set_bit(uint32_t* bm, bool set, int32_t v, int lane) {
+#if !GR_CLAIM_AGGREGATE
+  if (set) atomicOr(bm + (v >> 5), 1u << (v & 31));
+  return;
+#endif
+  const unsigned wkey = set ? (unsigned)v >> 5 : (0x80000000u | (unsigned)lane);
+  const unsigned peers = __match_any_sync(GR_FULL_MASK, wkey);
+  const uint32_t bits = __reduce_or_sync(peers, set ? 1u << (v & 31) : 0u);
+  if (set && lane == __ffs(peers) - 1) atomicOr(bm + (v >> 5), bits);
+}
+
+// Per-CTA staging of frontier appends in shared memory.  Warps append with
+// one shared-memory atomic per 32 candidates; at the end of the step the CTA
+// moves its entries to the global queue with ONE global atomicAdd, instead
+// of one per warp and strip (appends from every warp of the grid to a single
+// counter serialise in L2).  Entries beyond the shared capacity go straight
+// to global memory.
+#define GR_STAGE_CAP 2048
+struct GrStage {
+  int* buf;  // shared, GR_STAGE_CAP entries
+  int* cnt;  // shared
+  int* base; // shared
+  // one thread; a __syncthreads must follow before the first append
+  __device__ __forceinline__ void reset() { *cnt = 0; }
+  // all 32 lanes
+  __device__ __forceinline__ void append(int32_t* gq, int* glen, int64_t gcap, bool take,
+                                         int32_t v, int lane) {
+    const unsigned mask = __ballot_sync(GR_FULL_MASK, take);
+    if (mask == 0) return;
+    const int leader = __ffs(mask) - 1;
+    int b = 0;
+    if (lane == leader) b = atomicAdd(cnt, __popc(mask));
+    b = __shfl_sync(GR_FULL_MASK, b, leader);
+    const int pos = b + __popc(mask & ((1u << lane) - 1u));
+    const bool over = take && pos >= GR_STAGE_CAP;
+    if (take && !over) buf[pos] = v;
+    gr_warp_append(gq, glen, gcap, over, v, lane);
+  }
+  // every thread of the CTA
+  __device__ __forceinline__ void flush(int32_t* gq, int* glen, int64_t gcap) {
+    __syncthreads();
+    const int c = min(*cnt, GR_STAGE_CAP);
+    if (threadIdx.x == 0) *base = c > 0 ? atomicAdd(glen, c) : 0;
+    __syncthreads();
+    const int b = *base;
+    for (int i = threadIdx.x; i < c; i += blockDim.x)
+      if (b + i < gcap) gq[b + i] = buf[i];
+  }
+};
+
 // Warp-centric expansion of the rows of up to 32 sources (one per lane):
 // the warp scans the lanes' degrees and walks the concatenated edge ranges
 // 32 edges at a time; each lane finds the source of its edge with a 5-step
@@ -298,6 +420,87 @@ __device__ __forceinline__ void gr_warp_expand(const int32_t* __restrict__ R,
   }
 }
 
+// As gr_warp_expand, but U strips (32 * U edges) per round, in three passes
+// so that the memory accesses of the U strips overlap: first every lane
+// locates its U edges and loads their columns (streaming loads, so the
+// column stream does not evict the per-vertex state that lives in L2), then
+// `pre(active, e, v)`
+// issues the per-edge loads the functor needs (its results are returned),
+// and only then `edge(active, src, payload, e, v, pre_value)` runs for each
+// strip.  All lanes call both functors.
+template <int U, class Pre, class Edge>
+__device__ __forceinline__ void gr_warp_expand_u(const int32_t* __restrict__ R,
+                                                 const int32_t* __restrict__ C, bool valid,
+                                                 int32_t u, int beg, int deg, uint32_t payload,
+                                                 int lane, Pre&& pre, Edge&& edge) {
+  if (!valid) deg = 0;
+  int total;
+  const int off = gr_warp_excl_scan(deg, lane, &total);
+  for (int base = 0; base < total; base += 32 * U) {
+    int su[U], e[U], v[U];
+    uint32_t sp[U];
+    bool act[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int pos = base + k * 32 + lane;
+      int lo = 0;
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        const int cand = lo + step;
+        if (__shfl_sync(GR_FULL_MASK, off, cand) <= pos) lo = cand;
+      }
+      const int sbeg = __shfl_sync(GR_FULL_MASK, beg, lo);
+      const int soff = __shfl_sync(GR_FULL_MASK, off, lo);
+      su[k] = __shfl_sync(GR_FULL_MASK, u, lo);
+      sp[k] = __shfl_sync(GR_FULL_MASK, payload, lo);
+      act[k] = pos < total;
+      e[k] = sbeg + (pos - soff);
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) v[k] = act[k] ? GR_LDSTREAM(C + e[k]) : 0;
+    decltype(pre(true, 0, 0)) pv[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) pv[k] = pre(act[k], e[k], v[k]);
+#pragma unroll
+    for (int k = 0; k < U; ++k) edge(act[k], su[k], sp[k], e[k], v[k], pv[k]);
+  }
+}
+
+// Chunk counterpart of gr_warp_expand_u: edges [e0, e1) of row u.
+template <int U, class Pre, class Edge>
+__device__ __forceinline__ void gr_warp_chunk_u(const int32_t* __restrict__ C, int32_t u, int e0,
+                                                int e1, uint32_t payload, int lane, Pre&& pre,
+                                                Edge&& edge) {
+  for (int base = e0; base < e1; base += 32 * U) {
+    int e[U], v[U];
+    bool act[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      e[k] = base + k * 32 + lane;
+      act[k] = e[k] < e1;
+      v[k] = act[k] ? GR_LDSTREAM(C + e[k]) : 0;
+    }
+    decltype(pre(true, 0, 0)) pv[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) pv[k] = pre(act[k], e[k], v[k]);
+#pragma unroll
+    for (int k = 0; k < U; ++k) edge(act[k], u, payload, e[k], v[k], pv[k]);
+  }
+}
+
+// Default SSSP bucket width: 256 * mean weight / mean degree (at least 1).
+// Wide buckets trade a few repeated relaxations for far fewer grid-wide
+// steps, which is what bounds both low-diameter and mesh-like graphs here.
+inline uint32_t gr_default_delta(const gr_graph* g) {
+  if (g->m == 0 || g->nonisolated == 0) return 1;
+  double wmean = (double)g->weight_sum / (double)g->m;
+  double dmean = (double)g->m / (double)g->nonisolated;
+  double d = 256.0 * wmean / dmean;
+  if (d < 1.0) d = 1.0;
+  if (d > 1e9) d = 1e9;
+  return (uint32_t)d;
+}
+
 // Walk one edge chunk [e0, e1) of row u with the whole warp.
 template <class Edge>
 __device__ __forceinline__ void gr_warp_chunk(const int32_t* __restrict__ C, int32_t u, int e0,
@@ -325,6 +528,69 @@ __device__ __forceinline__ void gr_register_chunks(int2* chunks, int64_t cap, in
     else gr_set_status(status, GR_ERR_CAPACITY);
   }
 }
+
+// Per-CTA staging of split rows (rows of degree >= the split threshold
+// discovered in a step): the CTA reserves all their edge chunks with one
+// global atomicAdd at the end of the step instead of one per row.  Rows
+// beyond the shared capacity are registered directly.
+#define GR_BIG_STAGE_CAP 1024
+struct GrBigStage {
+  int* v;    // shared, GR_BIG_STAGE_CAP entries each
+  int* beg;
+  int* deg;
+  int* off;  // shared, GR_BIG_STAGE_CAP: chunk offset of each row within the CTA
+  int* cnt;  // shared
+  int* tot;  // shared [0] chunks of this CTA, [1] global base
+  __device__ __forceinline__ void reset() { *cnt = 0; }
+  // single lane
+  __device__ __forceinline__ void add(int2* chunks, int64_t cap, int* nchunk, int* nbig,
+                                      int32_t row, int b, int d, int* status) {
+    const int pos = atomicAdd(cnt, 1);
+    if (pos < GR_BIG_STAGE_CAP) {
+      v[pos] = row;
+      beg[pos] = b;
+      deg[pos] = d;
+    } else {
+      gr_register_chunks(chunks, cap, nchunk, nbig, row, b, d, status);
+    }
+  }
+  // every thread of the CTA: chunk ranges are reserved with shared-memory
+  // atomics, then one global atomicAdd places the CTA's block of chunks
+  __device__ __forceinline__ void flush(int2* chunks, int64_t cap, int* nchunk, int* nbig,
+                                        int* status) {
+    __syncthreads();
+    const int c = min(*cnt, GR_BIG_STAGE_CAP);
+    if (c == 0) return;  // uniform: every thread read the same count
+    if (threadIdx.x == 0) tot[0] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < c; i += blockDim.x)
+      off[i] = atomicAdd(&tot[0], (deg[i] + GR_CHUNK_EDGES - 1) / GR_CHUNK_EDGES);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tot[1] = atomicAdd(nchunk, tot[0]);
+      atomicAdd(nbig, c);
+    }
+    __syncthreads();
+    const int gbase = tot[1];
+    for (int i = threadIdx.x >> 5; i < c; i += blockDim.x >> 5) {  // a warp per row
+      const int nch = (deg[i] + GR_CHUNK_EDGES - 1) / GR_CHUNK_EDGES;
+      const int o = gbase + off[i];
+      for (int k = threadIdx.x & 31; k < nch; k += 32) {
+        if (o + k < cap) chunks[o + k] = make_int2(v[i], beg[i] + k * GR_CHUNK_EDGES);
+        else gr_set_status(status, GR_ERR_CAPACITY);
+      }
+    }
+  }
+};
+
+// Shared-memory arena for the staging buffers of a query body; a kernel
+// declares one and passes it to whichever body it runs (the batched kernel
+// holds both bodies but needs only one arena).
+struct GrArena {
+  int buf0[GR_STAGE_CAP];  // BFS next frontier / SSSP near frontier
+  int buf1[GR_STAGE_CAP];  // BFS unvisited list / SSSP far pile
+  int bv[GR_BIG_STAGE_CAP], bb[GR_BIG_STAGE_CAP], bd[GR_BIG_STAGE_CAP], bo[GR_BIG_STAGE_CAP];
+};
 
 // Warp-wide minimum of an unsigned.
 __device__ __forceinline__ unsigned gr_warp_min_u32(unsigned x) {

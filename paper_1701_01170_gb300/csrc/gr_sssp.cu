@@ -30,7 +30,8 @@ constexpr int NT = GR_PERSIST_THREADS;
 __global__ void __launch_bounds__(NT) sssp_persistent(SsspArgs a) {
   GridScope sc{a.ctl, a.status, a.spin, (int64_t)blockIdx.x * NT + threadIdx.x,
                (int64_t)gridDim.x * NT, 0u};
-  gr_sssp_body(a, sc);
+  __shared__ GrArena ar;
+  gr_sssp_body(a, sc, ar);
 }
 
 }  // namespace
@@ -46,15 +47,7 @@ extern "C" void gr_sssp_opts_default(gr_sssp_opts* o) {
 
 // Bucket width from the graph: about one warp's worth of average edges
 // (warp size * mean weight / mean degree), at least 1.
-static uint32_t default_delta(const gr_graph* g) {
-  if (g->m == 0 || g->nonisolated == 0) return 1;
-  double wmean = (double)g->weight_sum / (double)g->m;
-  double dmean = (double)g->m / (double)g->nonisolated;
-  double d = 32.0 * wmean / dmean;
-  if (d < 1.0) d = 1.0;
-  if (d > 1e9) d = 1e9;
-  return (uint32_t)d;
-}
+static uint32_t default_delta(const gr_graph* g) { return gr_default_delta(g); }
 
 extern "C" gr_status gr_sssp(const gr_graph* g, int32_t src, uint32_t* dist, int32_t* pred,
                              const gr_sssp_opts* opts, void* stream) {

@@ -8,6 +8,10 @@
 
 #include "gr_internal.cuh"
 
+#ifndef GR_RELAX_STRIPS
+#define GR_RELAX_STRIPS 2  // 32-edge strips a warp relaxes per round
+#endif
+
 struct SsspArgs {
   int32_t n;
   const int32_t* __restrict__ R;
@@ -34,7 +38,7 @@ struct SsspArgs {
 constexpr unsigned long long GR_KEY_INF = ~0ull;
 
 template <class S>
-__device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc) {
+__device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& ar) {
   const int lane = threadIdx.x & 31;
   const int64_t gtid = sc.tid;
   const int64_t gthreads = sc.nthreads;
@@ -69,6 +73,12 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc) {
   // step counters are read once per CTA and broadcast through shared memory
   __shared__ int s_nq, s_nch, s_flen;
   __shared__ unsigned s_fm;
+  __shared__ int s_ncnt, s_nbase, s_fcnt, s_fbase;
+  __shared__ unsigned s_farmin;
+  GrStage near_stage{ar.buf0, &s_ncnt, &s_nbase};
+  GrStage far_stage{ar.buf1, &s_fcnt, &s_fbase};
+  __shared__ int s_bcnt, s_btot[2];
+  GrBigStage bstage{ar.bv, ar.bb, ar.bd, ar.bo, &s_bcnt, s_btot};
   for (;; ++it) {
     const int s0 = it % 3, s1 = (it + 1) % 3, s2 = (it + 2) % 3;
     const int fs = fe % 3;
@@ -77,6 +87,10 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc) {
       s_nch = __ldcg(&ctl->nchunk[s0]);
       s_flen = __ldcg(&ctl->farlen[fs]);
       s_fm = __ldcg(&ctl->farmin[fs]);
+      near_stage.reset();
+      far_stage.reset();
+      bstage.reset();
+      s_farmin = UINT_MAX;
     }
     __syncthreads();
     const int nq = min(s_nq, a.n);
@@ -85,7 +99,7 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc) {
     const unsigned fm_step = s_fm;
     if (nq + nch == 0 && flen == 0) break;
     if (gtid == 0) {
-      gr_check_deadline(ctl, a.status, deadline);
+      if ((it & 63) == 0) gr_check_deadline(ctl, a.status, deadline);
       ctl->qlen[s2] = 0;
       ctl->nchunk[s2] = 0;
       ctl->nbig[s2] = 0;
@@ -105,29 +119,45 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc) {
         vdeg = __ldg(a.R + v + 1) - vbeg;
       }
       const bool big = take && vdeg >= a.big;
-      gr_warp_append(qn, &ctl->qlen[s1], a.n, take && !big, v, lane);
+      near_stage.append(qn, &ctl->qlen[s1], a.n, take && !big, v, lane);
       if (big)
-        gr_register_chunks(chn, a.chunk_cap, &ctl->nchunk[s1], &ctl->nbig[s1], v, vbeg, vdeg,
-                           a.status);
+        bstage.add(chn, a.chunk_cap, &ctl->nchunk[s1], &ctl->nbig[s1], v, vbeg, vdeg, a.status);
     };
     // join far pile `epoch` (once per epoch) — all lanes call this
+    // (a step only ever writes one far pile: epoch fe when relaxing, fe + 1
+    // when splitting)
+    const int fe_out = nq + nch > 0 ? fe : fe + 1;
     auto to_far = [&](bool take, int32_t v, unsigned d, int epoch) {
       if (take) take = atomicExch(&a.stamp_far[v], epoch) != epoch;
-      gr_warp_append(a.far[epoch & 1], &ctl->farlen[epoch % 3], a.n, take, v, lane);
+      far_stage.append(a.far[epoch & 1], &ctl->farlen[epoch % 3], a.n, take, v, lane);
       const unsigned mn = gr_warp_min_u32(take ? d : UINT_MAX);
-      if (lane == 0 && mn != UINT_MAX) atomicMin(&ctl->farmin[epoch % 3], mn);
+      if (lane == 0 && mn != UINT_MAX) atomicMin(&s_farmin, mn);
     };
 
     if (nq + nch > 0) {
       // ---- RELAX: advance + Update_Label / Set_Pred + Remove_Redundant ----
       const int32_t* q = a.q[it & 1];
       const int2* ch = a.ch[it & 1];
-      auto relax = [&](bool active, int32_t u, uint32_t du, int e, int32_t v) {
+      // pass 2: weight and current key of each edge's target
+      struct Pre {
+        uint32_t w;
+        unsigned long long cur;
+      };
+      auto pre = [&](bool active, int e, int32_t v) -> Pre {
+        Pre p{0u, 0ull};
+        if (active) {
+          p.w = GR_LDSTREAM(a.W + e);
+          p.cur = a.key[v];
+        }
+        return p;
+      };
+      // pass 3: Update_Label / Set_Pred as one 64-bit atomicMin on the key
+      auto relax = [&](bool active, int32_t u, uint32_t du, int, int32_t v, const Pre& p) {
         bool imp = false;
         unsigned long long nd = 0;
         if (active) {
           ++cnt.edges;
-          nd = (unsigned long long)du + __ldg(a.W + e);
+          nd = (unsigned long long)du + p.w;
           if (nd >= (unsigned long long)GR_INF_DIST) {
             // not representable: drop the candidate; whether a true distance
             // overflows is decided after convergence
@@ -137,7 +167,7 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc) {
             }
           } else {
             const unsigned long long cand = (nd << 32) | (unsigned)u;
-            if (cand < a.key[v]) imp = (atomicMin(&a.key[v], cand) >> 32) > nd;
+            if (cand < p.cur) imp = (atomicMin(&a.key[v], cand) >> 32) > nd;
             cnt.updates += imp;
           }
         }
@@ -147,7 +177,7 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc) {
       // warps take 32 near-frontier rows at a time: the first batch by warp
       // index, further batches from a counter (idle warps never touch it)
       for (int base = (int)gwarp * 32; base < nq;
-           base = (int)nwarps * 32 + gr_warp_grab(&ctl->work[s0], 32, lane)) {
+           base = gr_next_batch(base, nq, (int)nwarps * 32, &ctl->work[s0], 32, lane)) {
         const int i = base + lane;
         const bool valid = i < nq;
         int32_t u = 0;
@@ -160,15 +190,15 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc) {
           deg = __ldg(a.R + u + 1) - beg;
           du = (uint32_t)(a.key[u] >> 32);
         }
-        gr_warp_expand(a.R, a.C, valid, u, beg, deg, du, lane, relax);
+        gr_warp_expand_u<GR_RELAX_STRIPS>(a.R, a.C, valid, u, beg, deg, du, lane, pre, relax);
       }
       // then one 1024-edge chunk of a long row at a time
-      for (int c = (int)gwarp; c < nch; c = (int)nwarps + gr_warp_grab(&ctl->workc[s0], 1, lane)) {
+      for (int c = (int)gwarp; c < nch; c = gr_next_batch(c, nch, (int)nwarps, &ctl->workc[s0], 1, lane)) {
         const int2 cu = __ldcg(ch + c);
         const int e1 = min(cu.y + GR_CHUNK_EDGES, __ldg(a.R + cu.x + 1));
         const uint32_t du = (uint32_t)(a.key[cu.x] >> 32);
         if (lane == 0) ++cnt.verts;
-        gr_warp_chunk(a.C, cu.x, cu.y, e1, du, lane, relax);
+        gr_warp_chunk_u<GR_RELAX_STRIPS>(a.C, cu.x, cu.y, e1, du, lane, pre, relax);
       }
     } else {
       // ---- SPLIT: raise the threshold, move far entries below it to near --
@@ -185,7 +215,7 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc) {
       const int32_t* fp = a.far[fe & 1];
       // warps take 32 far entries at a time
       for (int base = (int)gwarp * 32; base < flen;
-           base = (int)nwarps * 32 + gr_warp_grab(&ctl->work[s0], 32, lane)) {
+           base = gr_next_batch(base, flen, (int)nwarps * 32, &ctl->work[s0], 32, lane)) {
         const int i = base + lane;
         int32_t v = 0;
         unsigned long long d = 0;
@@ -201,6 +231,10 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc) {
       T = Tn;
       ++fe;
     }
+    near_stage.flush(qn, &ctl->qlen[s1], a.n);
+    bstage.flush(chn, a.chunk_cap, &ctl->nchunk[s1], &ctl->nbig[s1], a.status);
+    far_stage.flush(a.far[fe_out & 1], &ctl->farlen[fe_out % 3], a.n);
+    if (threadIdx.x == 0 && s_farmin != UINT_MAX) atomicMin(&ctl->farmin[fe_out % 3], s_farmin);
     if (!sc.sync()) return;
   }
   // ---- overflow check: with every unrepresentable candidate dropped, a

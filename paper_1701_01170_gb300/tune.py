@@ -138,14 +138,14 @@ def tune_bfs(graph, sources, reps: int = 3, cache: TuneCache | None = None,
 
 
 def default_delta(graph) -> int:
-    """The library's own default bucket width (32 * mean weight / mean degree)."""
+    """The library's own default bucket width (256 * mean weight / mean degree)."""
     import numpy as np
     w = graph.W.to(dtype=__import__("torch").int64) & 0xFFFFFFFF
     m = max(graph.m, 1)
     deg = (graph.R[1:] - graph.R[:-1])
     nz = int((deg > 0).sum().item())
     mean_w = float(w.sum().item()) / m
-    return max(1, int(32.0 * mean_w / (m / max(nz, 1))))
+    return max(1, int(256.0 * mean_w / (m / max(nz, 1))))
 
 
 def tune_sssp(graph, sources, reps: int = 2, cache: TuneCache | None = None,

@@ -69,16 +69,17 @@ def test_switch_parameters_do_not_change_depths(gr, s16, do_a, do_b):
 def test_level_stats(gr, s16):
     import torch
     g, G = s16
-    stats = torch.full((3 * 64,), -7, dtype=torch.int32, device="cuda")
+    stats = torch.full((4 * 64,), -7, dtype=torch.int32, device="cuda")
     d, p = run_bfs(gr, G, 0, level_stats=stats.data_ptr(), max_levels=64)
     check(g, 0, d, p)
-    s = host(stats).reshape(64, 3)
+    s = host(stats).reshape(64, 4)
     levels = int(d.max()) + 1
     counts = np.bincount(d[d >= 0], minlength=levels)
     assert np.array_equal(s[:levels, 0], counts)        # frontier size per level
     deg = g.degrees()
     for L in range(levels):                              # m_f per level = sum of degrees
         assert s[L, 2] == min(int(deg[d == L].sum()), 2**31 - 1)
+    assert s[0, 3] >= 0 and (np.diff(s[:levels, 3]) >= 0).all()   # level start times
 
 
 def test_small_and_degenerate_graphs(gr):
