@@ -288,6 +288,17 @@ typedef struct gr_sssp_opts {
   int32_t blocks_per_sm; /* as in gr_bfs_opts                                  */
   uint32_t spin_limit;   /* as in gr_bfs_opts                                  */
   gr_workspace* ws;      /* NULL = the graph's default workspace              */
+  int32_t* level_stats;  /* optional device int32[4*max_levels]: per step
+                            (near rows, 1 if a SPLIT step, far-pile length,
+                            start time in ns after the first step)          */
+  int32_t max_levels;    /* capacity of level_stats in steps                  */
+  int32_t bulk_rows;     /* near frontiers of at least this many rows (an edge
+                            chunk of a split row counts as 8) are relaxed in
+                            bulk: atomics without return values plus a
+                            label-change bitmap, then one pass over the bitmap
+                            builds the next piles; smaller ones enqueue per
+                            edge.  0 = default (n / 64, at least 4096),
+                            < 0 = never                                      */
 } gr_sssp_opts;
 
 void gr_sssp_opts_default(gr_sssp_opts* o);

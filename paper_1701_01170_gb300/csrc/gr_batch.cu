@@ -174,6 +174,8 @@ __global__ void __launch_bounds__(BT) batch_kernel(BatchArgs b, SlotLayout L) {
       a.far[1] = (int32_t*)(base + L.far1);
       a.stamp_near = (int32_t*)(base + L.stn);
       a.stamp_far = (int32_t*)(base + L.stf);
+      a.touched = (uint32_t*)(base + L.vis);
+      a.bulk_rows = gr_default_bulk_rows(J.n);
       a.ctl = ctl;
       a.status = &b.job_status[J.index];
       a.src = J.src;

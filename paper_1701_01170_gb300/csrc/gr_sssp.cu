@@ -27,7 +27,10 @@ namespace {
 
 constexpr int NT = GR_PERSIST_THREADS;
 
-__global__ void __launch_bounds__(NT) sssp_persistent(SsspArgs a) {
+#ifndef GR_SSSP_MIN_BLOCKS
+#define GR_SSSP_MIN_BLOCKS 1
+#endif
+__global__ void __launch_bounds__(NT, GR_SSSP_MIN_BLOCKS) sssp_persistent(SsspArgs a) {
   GridScope sc{a.ctl, a.status, a.spin, (int64_t)blockIdx.x * NT + threadIdx.x,
                (int64_t)gridDim.x * NT, 0u};
   __shared__ GrArena ar;
@@ -43,6 +46,9 @@ extern "C" void gr_sssp_opts_default(gr_sssp_opts* o) {
   o->blocks_per_sm = 0;
   o->spin_limit = GR_DEFAULT_SPIN_LIMIT;
   o->ws = nullptr;
+  o->level_stats = nullptr;
+  o->max_levels = 0;
+  o->bulk_rows = 0;
 }
 
 // Bucket width from the graph: about one warp's worth of average edges
@@ -56,6 +62,7 @@ extern "C" gr_status gr_sssp(const gr_graph* g, int32_t src, uint32_t* dist, int
   gr_sssp_opts o;
   gr_sssp_opts_default(&o);
   if (opts) o = *opts;
+  if (o.max_levels < 0 || (o.max_levels > 0 && !o.level_stats)) return GR_ERR_INVALID_ARG;
   gr_workspace* ws = gr_resolve_ws(g, o.ws);
   if (!ws || ws->g != g || !ws->key) return GR_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -77,6 +84,8 @@ extern "C" gr_status gr_sssp(const gr_graph* g, int32_t src, uint32_t* dist, int
   a.far[1] = ws->far[1];
   a.stamp_near = ws->stamp_near;
   a.stamp_far = ws->stamp_far;
+  a.touched = o.bulk_rows < 0 ? nullptr : ws->visited;  // the BFS bitmap is free here
+  a.bulk_rows = o.bulk_rows > 0 ? o.bulk_rows : gr_default_bulk_rows(g->n);
   a.ctl = ws->ctl;
   a.status = ws->status;
   a.src = src;
@@ -84,6 +93,8 @@ extern "C" gr_status gr_sssp(const gr_graph* g, int32_t src, uint32_t* dist, int
   a.big = o.big_degree > 0 ? (o.big_degree < 32 ? 32 : o.big_degree) : GR_DEFAULT_BIG_DEGREE;
   a.track_deg = g->max_degree >= a.big;
   a.spin = o.spin_limit ? o.spin_limit : GR_DEFAULT_SPIN_LIMIT;
+  a.level_stats = o.level_stats;
+  a.max_levels = o.max_levels;
 
   const int blocks = gr_launch_blocks((const void*)sssp_persistent, NT, 0, g->num_sms,
                                       o.blocks_per_sm);

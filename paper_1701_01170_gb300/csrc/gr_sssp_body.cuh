@@ -11,6 +11,19 @@
 #ifndef GR_RELAX_STRIPS
 #define GR_RELAX_STRIPS 2  // 32-edge strips a warp relaxes per round
 #endif
+#ifndef GR_BULK_STRIPS
+#define GR_BULK_STRIPS 2  // 32-edge strips a warp relaxes per round in bulk steps
+#endif
+// Bulk steps (fire-and-forget atomics and a label-change bitmap, then one
+// pass over the bitmap builds the next piles) pay one extra barrier and a
+// pass over n bits, so by default they start at n / GR_BULK_DIVISOR near rows
+// (a chunk counting as 8), and at GR_BULK_MIN_ROWS at least.
+#define GR_BULK_DIVISOR 64
+#define GR_BULK_MIN_ROWS 4096
+__host__ __device__ inline int32_t gr_default_bulk_rows(int64_t n) {
+  const int64_t r = n / GR_BULK_DIVISOR;
+  return (int32_t)(r > GR_BULK_MIN_ROWS ? r : GR_BULK_MIN_ROWS);
+}
 
 struct SsspArgs {
   int32_t n;
@@ -26,6 +39,8 @@ struct SsspArgs {
   int32_t* far[2];
   int32_t* stamp_near;
   int32_t* stamp_far;
+  uint32_t* touched;  // n-bit label-change bitmap of bulk steps (NULL: no bulk steps)
+  int32_t bulk_rows;  // near rows (a chunk counts as 8) from which a step runs in bulk
   GrCtl* ctl;
   int* status;
   int32_t src;
@@ -33,6 +48,8 @@ struct SsspArgs {
   int big;
   int track_deg;
   unsigned spin;
+  int32_t* level_stats;
+  int32_t max_levels;
 };
 
 constexpr unsigned long long GR_KEY_INF = ~0ull;
@@ -51,6 +68,9 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
     a.stamp_near[v] = v == a.src ? 0 : -1;
     a.stamp_far[v] = -1;
   }
+  const int nwords = (int)(((int64_t)a.n + 31) >> 5);
+  if (a.touched)
+    for (int64_t w = gtid; w < nwords; w += gthreads) a.touched[w] = 0u;
   if (gtid == 0) {
     const int beg = a.R[a.src], deg = a.R[a.src + 1] - beg;
     if (a.track_deg && deg >= a.big)
@@ -71,7 +91,7 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
   GrCounters cnt;
   bool ovf_seen = false;
   // step counters are read once per CTA and broadcast through shared memory
-  __shared__ int s_nq, s_nch, s_flen;
+  __shared__ int s_nq, s_nch, s_nbig, s_flen;
   __shared__ unsigned s_fm;
   __shared__ int s_ncnt, s_nbase, s_fcnt, s_fbase;
   __shared__ unsigned s_farmin;
@@ -85,6 +105,7 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
     if (threadIdx.x == 0) {
       s_nq = __ldcg(&ctl->qlen[s0]);
       s_nch = __ldcg(&ctl->nchunk[s0]);
+      s_nbig = __ldcg(&ctl->nbig[s0]);
       s_flen = __ldcg(&ctl->farlen[fs]);
       s_fm = __ldcg(&ctl->farmin[fs]);
       near_stage.reset();
@@ -100,19 +121,27 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
     if (nq + nch == 0 && flen == 0) break;
     if (gtid == 0) {
       if ((it & 63) == 0) gr_check_deadline(ctl, a.status, deadline);
+      if (a.level_stats && it < a.max_levels) {
+        a.level_stats[4 * it] = nq + s_nbig;
+        a.level_stats[4 * it + 1] = nq + nch == 0;
+        a.level_stats[4 * it + 2] = flen;
+        // start of this step in ns after the first step started
+        a.level_stats[4 * it + 3] =
+            (int)min(gr_globaltimer() - (deadline - GR_TIME_LIMIT_NS), (unsigned long long)INT_MAX);
+      }
       ctl->qlen[s2] = 0;
       ctl->nchunk[s2] = 0;
       ctl->nbig[s2] = 0;
       ctl->work[s2] = 0;
       ctl->workc[s2] = 0;
+      ctl->workb[s2] = 0;
     }
     int32_t* qn = a.q[(it + 1) & 1];
     int2* chn = a.ch[(it + 1) & 1];
     const int next_stamp = it + 1;
 
-    // join the next near frontier (once per step) — all lanes call this
-    auto to_near = [&](bool take, int32_t v) {
-      if (take) take = atomicExch(&a.stamp_near[v], next_stamp) != next_stamp;
+    // append to the next near frontier — all lanes call this
+    auto near_append = [&](bool take, int32_t v) {
       int vbeg = 0, vdeg = 0;
       if (take && a.track_deg) {
         vbeg = __ldg(a.R + v);
@@ -122,6 +151,11 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
       near_stage.append(qn, &ctl->qlen[s1], a.n, take && !big, v, lane);
       if (big)
         bstage.add(chn, a.chunk_cap, &ctl->nchunk[s1], &ctl->nbig[s1], v, vbeg, vdeg, a.status);
+    };
+    // join the next near frontier (once per step) — all lanes call this
+    auto to_near = [&](bool take, int32_t v) {
+      if (take) take = atomicExch(&a.stamp_near[v], next_stamp) != next_stamp;
+      near_append(take, v);
     };
     // join far pile `epoch` (once per epoch) — all lanes call this
     // (a step only ever writes one far pile: epoch fe when relaxing, fe + 1
@@ -134,7 +168,102 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
       if (lane == 0 && mn != UINT_MAX) atomicMin(&s_farmin, mn);
     };
 
-    if (nq + nch > 0) {
+    const bool bulk = a.touched && nq + 8ll * nch >= a.bulk_rows;
+    if (bulk) {
+      // ---- bulk RELAX: Update_Label / Set_Pred as fire-and-forget 64-bit
+      // atomicMin, plus one bit per changed label; no return values and no
+      // per-edge queue work.  Labels are read from L2 so that a bit is set
+      // only for a label that this step really lowers.
+      const int32_t* q = a.q[it & 1];
+      const int2* ch = a.ch[it & 1];
+      struct PreB {
+        uint32_t w;
+        unsigned long long cur;
+      };
+      auto pre = [&](bool active, int e, int32_t v) -> PreB {
+        PreB p{0u, 0ull};
+        if (active) {
+          p.w = GR_LDSTREAM(a.W + e);
+          p.cur = __ldcg(a.key + v);
+        }
+        return p;
+      };
+      auto relax = [&](bool active, int32_t u, uint32_t du, int, int32_t v, const PreB& p) {
+        bool hit = false;
+        if (active) {
+          ++cnt.edges;
+          const unsigned long long nd = (unsigned long long)du + p.w;
+          if (nd >= (unsigned long long)GR_INF_DIST) {
+            if (!ovf_seen) {
+              ovf_seen = true;
+              atomicExch(&ctl->ovf_pending, 1);
+            }
+          } else {
+            const unsigned long long cand = (nd << 32) | (unsigned)u;
+            if (cand < p.cur) {
+              atomicMin(&a.key[v], cand);
+              hit = true;
+            }
+          }
+        }
+        if (hit) atomicOr(a.touched + (v >> 5), 1u << (v & 31));
+      };
+      for (int base = (int)gwarp * 32; base < nq;
+           base = gr_next_batch(base, nq, (int)nwarps * 32, &ctl->work[s0], 32, lane)) {
+        const int i = base + lane;
+        const bool valid = i < nq;
+        int32_t u = 0;
+        int beg = 0, deg = 0;
+        uint32_t du = 0;
+        if (valid) {
+          ++cnt.verts;
+          u = __ldcg(q + i);
+          beg = __ldg(a.R + u);
+          deg = __ldg(a.R + u + 1) - beg;
+          du = (uint32_t)(__ldcg(a.key + u) >> 32);
+        }
+        gr_warp_expand_u<GR_BULK_STRIPS>(a.R, a.C, valid, u, beg, deg, du, lane, pre, relax);
+      }
+      for (int c = (int)gwarp; c < nch; c = gr_next_batch(c, nch, (int)nwarps, &ctl->workc[s0], 1, lane)) {
+        const int2 cu = __ldcg(ch + c);
+        const int e1 = min(cu.y + GR_CHUNK_EDGES, __ldg(a.R + cu.x + 1));
+        const uint32_t du = (uint32_t)(__ldcg(a.key + cu.x) >> 32);
+        if (lane == 0) ++cnt.verts;
+        gr_warp_chunk_u<GR_BULK_STRIPS>(a.C, cu.x, cu.y, e1, du, lane, pre, relax);
+      }
+      if (!sc.sync()) return;
+      // ---- collect: every vertex whose label dropped in this step joins
+      // the near frontier (dist < T) or, once per epoch, the far pile.  A
+      // warp owns 32 bitmap words at a time and clears them.
+      for (int wb = (int)gwarp * 32; wb < nwords;
+           wb = gr_next_batch(wb, nwords, (int)nwarps * 32, &ctl->workb[s0], 32, lane)) {
+        const int w = wb + lane;
+        uint32_t word = w < nwords ? __ldcg(a.touched + w) : 0u;
+        if (word) a.touched[w] = 0u;
+        unsigned nz = __ballot_sync(GR_FULL_MASK, word != 0u);
+        while (nz) {
+          const int j = __ffs(nz) - 1;
+          nz &= nz - 1u;
+          const uint32_t bits = __shfl_sync(GR_FULL_MASK, word, j);
+          const bool mine = (bits >> lane) & 1u;
+          const int32_t v = (wb + j) * 32 + lane;
+          unsigned d = 0;
+          if (mine) {
+            ++cnt.updates;
+            d = (unsigned)(__ldcg(a.key + v) >> 32);
+          }
+          near_append(mine && d < T, v);
+          bool far = mine && d >= T;
+          if (far) {
+            far = a.stamp_far[v] != fe;  // this thread owns v in this pass
+            if (far) a.stamp_far[v] = fe;
+          }
+          far_stage.append(a.far[fe & 1], &ctl->farlen[fe % 3], a.n, far, v, lane);
+          const unsigned mn = gr_warp_min_u32(far ? d : UINT_MAX);
+          if (lane == 0 && mn != UINT_MAX) atomicMin(&s_farmin, mn);
+        }
+      }
+    } else if (nq + nch > 0) {
       // ---- RELAX: advance + Update_Label / Set_Pred + Remove_Redundant ----
       const int32_t* q = a.q[it & 1];
       const int2* ch = a.ch[it & 1];

@@ -66,7 +66,7 @@ def test_option_struct_layouts_match_header(lib_path):
     s = gr.sssp_opts()
     assert s.delta == 0 and s.big_degree > 0
     assert ctypes.sizeof(gr.gr_bfs_opts) == 48
-    assert ctypes.sizeof(gr.gr_sssp_opts) == 24
+    assert ctypes.sizeof(gr.gr_sssp_opts) == 40
     assert ctypes.sizeof(gr.gr_bfs_state) == 24
     assert ctypes.sizeof(gr.gr_sssp_state) == 16
 
@@ -78,3 +78,33 @@ def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(_build, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="missing"):
         gr.load()
+
+
+def test_ctypes_mirrors_match_the_compiled_header(tmp_path):
+    # compile gr.h with the host C compiler and compare every struct's size
+    # and field offsets with the ctypes mirror of the Python binding
+    import shutil
+
+    import paper_1701_01170_gb300 as gr
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [gr.gr_run_stats, gr.gr_bfs_state, gr.gr_sssp_state, gr.gr_bfs_opts,
+               gr.gr_sssp_opts, gr.gr_msbfs_opts, gr.gr_job, gr.gr_batch_opts]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "gr.h"', "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f in st._fields_:
+            lines.append(f'  printf("{name}.{f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-std=c11", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    for st in structs:
+        name = st.__name__
+        assert int(got[name]) == ctypes.sizeof(st), name
+        for f in st._fields_:
+            assert int(got[f"{name}.{f[0]}"]) == getattr(st, f[0]).offset, (name, f[0])

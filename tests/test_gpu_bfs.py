@@ -102,6 +102,52 @@ def test_small_and_degenerate_graphs(gr):
         G.close()
 
 
+@pytest.mark.parametrize("direction", [0, 1])
+def test_mesh_graph(gr, direction):
+    # hundreds of levels with frontiers of a few hundred vertices
+    g = gg.grid(128, 0.1, seed=4)
+    G = gr.Graph.from_csr(g)
+    for src in (0, 8256):
+        d, p = run_bfs(gr, G, src, direction=direction)
+        check(g, src, d, p)
+    G.close()
+
+
+def dumbbell(path_len=100, leaves=40000):
+    """path -> hub A -> `leaves` leaves -> hub B -> path: small, huge, small frontiers."""
+    a = path_len - 1
+    b = path_len + leaves
+    n = b + path_len
+    pairs = [(i, i + 1) for i in range(path_len - 1)]
+    pairs += [(a, path_len + i) for i in range(leaves)]
+    pairs += [(path_len + i, b) for i in range(leaves)]
+    pairs += [(b + i, b + i + 1) for i in range(path_len - 1)]
+    return undirected(n, pairs)
+
+
+@pytest.mark.parametrize("direction", [0, 1])
+def test_frontier_grows_and_shrinks(gr, direction):
+    # tiny frontiers along the paths, 40000 vertices (80000 edges) at the
+    # leaves: with direction 0 some levels run pull and others push
+    import torch
+    g = dumbbell()
+    G = gr.Graph.from_csr(g)
+    levels = 201   # path 0..99, the leaves, hub B, then depths 102..200
+    stats = torch.full((4 * 256,), -7, dtype=torch.int32, device="cuda")
+    d, p = run_bfs(gr, G, 0, direction=direction, level_stats=stats.data_ptr(), max_levels=256)
+    check(g, 0, d, p)
+    s = host(stats).reshape(256, 4)
+    assert int(d.max()) + 1 == levels
+    assert np.array_equal(s[:levels, 0], np.bincount(d, minlength=levels))
+    assert (np.diff(s[:levels, 3]) >= 0).all()
+    if direction == 0:
+        assert s[:levels, 1].any() and not s[:levels, 1].all()
+    for src in (g.n - 1, 100 + 7):
+        d, p = run_bfs(gr, G, src, direction=direction)
+        check(g, src, d, p)
+    G.close()
+
+
 def test_directed_graph_push_only(gr):
     rng = np.random.default_rng(3)
     n = 3000

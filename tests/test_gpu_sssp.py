@@ -55,6 +55,37 @@ def test_rmat_s16_deltas_agree(gr, s16w, delta):
         check(g, src, d, p)
 
 
+def test_step_stats(gr, s16w):
+    import torch
+    g, G = s16w
+    cap = 4096
+    stats = torch.full((4 * cap,), -7, dtype=torch.int32, device="cuda")
+    src = gg.max_degree_vertex(g)
+    for delta in (7, 64):
+        stats.fill_(-7)
+        d, p = run_sssp(gr, G, src, delta=delta, level_stats=stats.data_ptr(), max_levels=cap)
+        check(g, src, d, p)
+        steps = gr.gr_last_run_stats(G.handle)["levels"]
+        assert 0 < steps < cap
+        s = host(stats).reshape(cap, 4)[:steps]
+        assert s[0, 0] == 1 and s[0, 1] == 0 and s[0, 2] == 0    # the source alone
+        split = s[:, 1] == 1
+        assert (s[split, 0] == 0).all() and (s[split, 2] > 0).all()  # splits drain the far pile
+        assert (s[~split, 0] > 0).all()
+        assert (np.diff(s[:, 3]) >= 0).all()
+        assert (host(stats).reshape(cap, 4)[steps:] == -7).all()
+
+
+@pytest.mark.parametrize("bulk", [-1, 1, 4096])
+@pytest.mark.parametrize("delta", [0, 7, 1 << 30])
+def test_bulk_and_per_edge_steps_agree(gr, s16w, bulk, delta):
+    # bulk = 1: every relax step runs in bulk; -1: none does; 4096: mixed
+    g, G = s16w
+    for src in (gg.max_degree_vertex(g), 4321):
+        d, p = run_sssp(gr, G, src, delta=delta, bulk_rows=bulk)
+        check(g, src, d, p)
+
+
 @pytest.mark.parametrize("big", [32, 1 << 30])
 def test_split_thresholds_agree(gr, s16w, big):
     g, G = s16w
@@ -66,8 +97,9 @@ def test_grid_small_wide_weights(gr):
     g = gg.grid_weighted(200, 0.1, seed=3)
     G = gr.Graph.from_csr(g)
     for delta in (0, 100, 5000):
-        d, p = run_sssp(gr, G, 0, delta=delta)
-        check(g, 0, d, p)
+        for bulk in (0, 1):
+            d, p = run_sssp(gr, G, 0, delta=delta, bulk_rows=bulk)
+            check(g, 0, d, p)
 
 
 def test_constant_weight_is_scaled_bfs(gr):
@@ -90,8 +122,9 @@ def test_degenerate_graphs(gr):
         G = gr.Graph.from_csr(g)
         for src in {0, g.n - 1}:
             for big in (32, 1024):
-                d, p = run_sssp(gr, G, src, big_degree=big)
-                check(g, src, d, p)
+                for bulk in (-1, 1):
+                    d, p = run_sssp(gr, G, src, big_degree=big, bulk_rows=bulk)
+                    check(g, src, d, p)
         G.close()
 
 
@@ -99,11 +132,13 @@ def test_overflow_detected(gr):
     g = undirected(4, [(0, 1), (1, 2), (2, 3)])
     g.W = np.full(g.m, 2**31, np.uint32)
     G = gr.Graph.from_csr(g)
-    run_sssp(gr, G, 0, expect=gr.GR_ERR_OVERFLOW)
+    for bulk in (-1, 1):
+        run_sssp(gr, G, 0, expect=gr.GR_ERR_OVERFLOW, bulk_rows=bulk)
     g.W = np.full(g.m, 2**30, np.uint32)
     G2 = gr.Graph.from_csr(g)
-    d, p = run_sssp(gr, G2, 0)
-    check(g, 0, d, p)
+    for bulk in (-1, 1):
+        d, p = run_sssp(gr, G2, 0, bulk_rows=bulk)
+        check(g, 0, d, p)
 
 
 def test_sssp_needs_weights(gr):
