@@ -49,6 +49,11 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
   const int64_t gtid = sc.tid;
   const int64_t gthreads = sc.nthreads;
   const int64_t gwarp = gtid >> 5, nwarps = gthreads >> 5;
+  // Static-first batches are dealt out across CTAs: batch k of a step goes to
+  // CTA k mod (number of CTAs), so a small step spreads over every SM instead
+  // of filling the first CTAs (and their staging buffers) alone.
+  const int wpc = (int)(blockDim.x >> 5);
+  const int swarp = (int)((gwarp % wpc) * (nwarps / wpc) + gwarp / wpc);
   GrCtl* ctl = a.ctl;
   // ---- Set_Problem_Data: depth -1 / pred -1, the source at depth 0 ------
   for (int64_t v = gtid; v < a.n; v += gthreads) {
@@ -188,7 +193,7 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
       };
       // warps take 32 frontier rows at a time: the first batch by warp index,
       // further batches from a counter (idle warps never touch it)
-      for (int base = (int)gwarp * 32; base < nq;
+      for (int base = swarp * 32; base < nq;
            base = gr_next_batch(base, nq, (int)nwarps * 32, &ctl->work[s0], 32, lane)) {
         const int i = base + lane;
         const bool valid = i < nq;
@@ -203,7 +208,7 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
         gr_warp_expand_u<GR_VISIT_STRIPS>(a.R, a.C, valid, u, beg, deg, 0u, lane, pre, visit);
       }
       // then one 1024-edge chunk of a long row at a time
-      for (int c = (int)gwarp; c < nch; c = gr_next_batch(c, nch, (int)nwarps, &ctl->workc[s0], 1, lane)) {
+      for (int c = swarp; c < nch; c = gr_next_batch(c, nch, (int)nwarps, &ctl->workc[s0], 1, lane)) {
         const int2 cu = __ldcg(ch + c);
         const int e1 = min(cu.y + GR_CHUNK_EDGES, __ldg(a.R + cu.x + 1));
         if (lane == 0) ++cnt.verts;
@@ -273,7 +278,7 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
         // the previous level was a pull level: walk its unvisited list
         const int32_t* cand = a.ulist[L & 1];
         const int nc = min(s_nu, a.n);
-        for (int base = (int)gwarp * 32; base < nc;
+        for (int base = swarp * 32; base < nc;
              base = gr_next_batch(base, nc, (int)nwarps * 32, &ctl->work[s0], 32, lane)) {
           const int i = base + lane;
           const bool valid = i < nc;
@@ -294,7 +299,7 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
       } else {
         // first pull level: the unvisited set is the complement of the visited
         // bitmap; warps take GR_PULL_WORDS words (32 vertices each) at a time
-        for (int wb = (int)gwarp * GR_PULL_WORDS; wb < a.nwords;
+        for (int wb = swarp * GR_PULL_WORDS; wb < a.nwords;
              wb = gr_next_batch(wb, a.nwords, (int)nwarps * GR_PULL_WORDS, &ctl->work[s0],
                                 GR_PULL_WORDS, lane)) {
           const int we = min(wb + GR_PULL_WORDS, a.nwords);

@@ -36,7 +36,9 @@
 
 // Library defaults (tunable per call through gr_bfs_opts / gr_sssp_opts).
 #define GR_DEFAULT_BIG_DEGREE 1024   // rows >= this are split into edge chunks
+#ifndef GR_CHUNK_EDGES
 #define GR_CHUNK_EDGES 256           // edges per chunk of a split row
+#endif
 #define GR_DEFAULT_SPIN_LIMIT (1u << 24)
 #define GR_TIME_LIMIT_NS (60ull * 1000000000ull)  // persistent kernels give up after 60 s
 #define GR_PERSIST_THREADS 512

@@ -60,6 +60,11 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
   const int64_t gtid = sc.tid;
   const int64_t gthreads = sc.nthreads;
   const int64_t gwarp = gtid >> 5, nwarps = gthreads >> 5;
+  // Static-first batches are dealt out across CTAs: batch k of a step goes to
+  // CTA k mod (number of CTAs), so a small step spreads over every SM instead
+  // of filling the first CTAs (and their staging buffers) alone.
+  const int wpc = (int)(blockDim.x >> 5);
+  const int swarp = (int)((gwarp % wpc) * (nwarps / wpc) + gwarp / wpc);
   GrCtl* ctl = a.ctl;
 
   // ---- Set_Problem_Data (Alg. 1): labels infinite, preds -1, root 0 -----
@@ -208,7 +213,7 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
         }
         if (hit) atomicOr(a.touched + (v >> 5), 1u << (v & 31));
       };
-      for (int base = (int)gwarp * 32; base < nq;
+      for (int base = swarp * 32; base < nq;
            base = gr_next_batch(base, nq, (int)nwarps * 32, &ctl->work[s0], 32, lane)) {
         const int i = base + lane;
         const bool valid = i < nq;
@@ -224,7 +229,7 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
         }
         gr_warp_expand_u<GR_BULK_STRIPS>(a.R, a.C, valid, u, beg, deg, du, lane, pre, relax);
       }
-      for (int c = (int)gwarp; c < nch; c = gr_next_batch(c, nch, (int)nwarps, &ctl->workc[s0], 1, lane)) {
+      for (int c = swarp; c < nch; c = gr_next_batch(c, nch, (int)nwarps, &ctl->workc[s0], 1, lane)) {
         const int2 cu = __ldcg(ch + c);
         const int e1 = min(cu.y + GR_CHUNK_EDGES, __ldg(a.R + cu.x + 1));
         const uint32_t du = (uint32_t)(__ldcg(a.key + cu.x) >> 32);
@@ -235,7 +240,7 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
       // ---- collect: every vertex whose label dropped in this step joins
       // the near frontier (dist < T) or, once per epoch, the far pile.  A
       // warp owns 32 bitmap words at a time and clears them.
-      for (int wb = (int)gwarp * 32; wb < nwords;
+      for (int wb = swarp * 32; wb < nwords;
            wb = gr_next_batch(wb, nwords, (int)nwarps * 32, &ctl->workb[s0], 32, lane)) {
         const int w = wb + lane;
         uint32_t word = w < nwords ? __ldcg(a.touched + w) : 0u;
@@ -305,7 +310,7 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
       };
       // warps take 32 near-frontier rows at a time: the first batch by warp
       // index, further batches from a counter (idle warps never touch it)
-      for (int base = (int)gwarp * 32; base < nq;
+      for (int base = swarp * 32; base < nq;
            base = gr_next_batch(base, nq, (int)nwarps * 32, &ctl->work[s0], 32, lane)) {
         const int i = base + lane;
         const bool valid = i < nq;
@@ -322,7 +327,7 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
         gr_warp_expand_u<GR_RELAX_STRIPS>(a.R, a.C, valid, u, beg, deg, du, lane, pre, relax);
       }
       // then one 1024-edge chunk of a long row at a time
-      for (int c = (int)gwarp; c < nch; c = gr_next_batch(c, nch, (int)nwarps, &ctl->workc[s0], 1, lane)) {
+      for (int c = swarp; c < nch; c = gr_next_batch(c, nch, (int)nwarps, &ctl->workc[s0], 1, lane)) {
         const int2 cu = __ldcg(ch + c);
         const int e1 = min(cu.y + GR_CHUNK_EDGES, __ldg(a.R + cu.x + 1));
         const uint32_t du = (uint32_t)(a.key[cu.x] >> 32);
@@ -343,7 +348,7 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
       }
       const int32_t* fp = a.far[fe & 1];
       // warps take 32 far entries at a time
-      for (int base = (int)gwarp * 32; base < flen;
+      for (int base = swarp * 32; base < flen;
            base = gr_next_batch(base, flen, (int)nwarps * 32, &ctl->work[s0], 32, lane)) {
         const int i = base + lane;
         int32_t v = 0;
