@@ -274,56 +274,92 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
         // a vertex that can still be discovered stays on the unvisited list
         if (unext) ustage.append(unext, &ctl->ulen[s1], a.n, valid && found < 0 && deg > 0, v, lane);
       };
-      if (list_pull) {
-        // the previous level was a pull level: walk its unvisited list
-        const int32_t* cand = a.ulist[L & 1];
-        const int nc = min(s_nu, a.n);
-        for (int base = swarp * 32; base < nc;
-             base = gr_next_batch(base, nc, (int)nwarps * 32, &ctl->work[s0], 32, lane)) {
-          const int i = base + lane;
-          const bool valid = i < nc;
-          int32_t v = 0, found = -1;
-          int beg = 0, deg = 0;
-          if (valid) {
+      // A lane holds GR_PULL_WORDS candidates at once: their row bounds and
+      // first neighbours are loaded together (independent loads in flight),
+      // then each candidate whose first neighbour is not in the frontier
+      // continues with find_parent from its second neighbour.
+      constexpr int K = GR_PULL_WORDS;
+      auto probe = [&](const bool (&cand)[K], const int32_t (&v)[K], int (&beg)[K], int (&deg)[K],
+                       int32_t (&f0)[K]) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          beg[k] = 0;
+          deg[k] = 0;
+          if (cand[k]) {
             ++cnt.verts;
-            v = __ldcg(cand + i);
-            beg = __ldg(a.R + v);
-            deg = __ldg(a.R + v + 1) - beg;
+            beg[k] = __ldg(a.R + v[k]);
+            deg[k] = __ldg(a.R + v[k] + 1) - beg[k];
           }
-          found = find_parent(valid, beg, deg);
-          // list entries are distinct vertices: set their bits, one atomic per word
-          gr_warp_set_bit(a.visited, found >= 0, v, lane);
-          gr_warp_set_bit(fnext, found >= 0, v, lane);
-          commit(valid, v, found, beg, deg);
+        }
+        int32_t u0[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          u0[k] = cand[k] && deg[k] > 0 ? __ldg(a.C + beg[k]) : -1;
+          if (u0[k] >= 0) ++cnt.edges;
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          f0[k] = u0[k] >= 0 && ((fcur[u0[k] >> 5] >> (u0[k] & 31)) & 1u) ? u0[k] : -1;
+      };
+      if (list_pull) {
+        // the previous level was a pull level: walk its unvisited list,
+        // K * 32 entries per warp and batch
+        const int32_t* cl = a.ulist[L & 1];
+        const int nc = min(s_nu, a.n);
+        for (int base = swarp * 32 * K; base < nc;
+             base = gr_next_batch(base, nc, (int)nwarps * 32 * K, &ctl->work[s0], 32 * K, lane)) {
+          bool cand[K];
+          int32_t v[K], f0[K];
+          int beg[K], deg[K];
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const int i = base + k * 32 + lane;
+            cand[k] = i < nc;
+            v[k] = cand[k] ? __ldcg(cl + i) : 0;
+          }
+          probe(cand, v, beg, deg, f0);
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            int32_t found = f0[k];
+            const int32_t rest = find_parent(cand[k] && found < 0 && deg[k] > 1, beg[k] + 1, deg[k] - 1);
+            if (found < 0) found = rest;
+            // list entries are distinct vertices: set their bits, one atomic per word
+            gr_warp_set_bit(a.visited, found >= 0, v[k], lane);
+            gr_warp_set_bit(fnext, found >= 0, v[k], lane);
+            commit(cand[k], v[k], found, beg[k], deg[k]);
+          }
         }
       } else {
         // first pull level: the unvisited set is the complement of the visited
-        // bitmap; warps take GR_PULL_WORDS words (32 vertices each) at a time
-        for (int wb = swarp * GR_PULL_WORDS; wb < a.nwords;
-             wb = gr_next_batch(wb, a.nwords, (int)nwarps * GR_PULL_WORDS, &ctl->work[s0],
-                                GR_PULL_WORDS, lane)) {
-          const int we = min(wb + GR_PULL_WORDS, a.nwords);
-          for (int64_t w = wb; w < we; ++w) {
-            const uint32_t word = a.visited[w];
-            if (word == 0xffffffffu) continue;
-            const int64_t v64 = w * 32 + lane;
-            const int32_t v = (int32_t)v64;
-            const bool cand = v64 < a.n && !((word >> lane) & 1u);
-            int32_t found = -1;
-            int beg = 0, deg = 0;
-            if (cand) {
-              ++cnt.verts;
-              beg = __ldg(a.R + v);
-              deg = __ldg(a.R + v + 1) - beg;
-            }
-            found = find_parent(cand, beg, deg);
+        // bitmap; warps take K words (32 vertices each) at a time
+        for (int wb = swarp * K; wb < a.nwords;
+             wb = gr_next_batch(wb, a.nwords, (int)nwarps * K, &ctl->work[s0], K, lane)) {
+          const uint32_t wl = lane < K && wb + lane < a.nwords ? a.visited[wb + lane] : 0xffffffffu;
+          uint32_t word[K];
+          bool cand[K];
+          int32_t v[K], f0[K];
+          int beg[K], deg[K];
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            word[k] = __shfl_sync(GR_FULL_MASK, wl, k);
+            const int64_t v64 = (int64_t)(wb + k) * 32 + lane;
+            v[k] = (int32_t)v64;
+            cand[k] = v64 < a.n && !((word[k] >> lane) & 1u);
+          }
+          probe(cand, v, beg, deg, f0);
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            if (word[k] == 0xffffffffu) continue;  // warp-uniform
+            int32_t found = f0[k];
+            const int32_t rest = find_parent(cand[k] && found < 0 && deg[k] > 1, beg[k] + 1, deg[k] - 1);
+            if (found < 0) found = rest;
             // the warp owns this word: visited and next-frontier bits by ballot
             const unsigned hit = __ballot_sync(GR_FULL_MASK, found >= 0);
             if (hit != 0u && lane == 0) {
-              a.visited[w] = word | hit;
-              fnext[w] = hit;
+              a.visited[wb + k] = word[k] | hit;
+              fnext[wb + k] = hit;
             }
-            commit(cand, v, found, beg, deg);
+            commit(cand[k], v[k], found, beg[k], deg[k]);
           }
         }
       }

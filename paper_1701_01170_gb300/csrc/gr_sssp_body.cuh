@@ -9,11 +9,12 @@
 #include "gr_internal.cuh"
 
 #ifndef GR_RELAX_STRIPS
-#define GR_RELAX_STRIPS 2  // 32-edge strips a warp relaxes per round
+#define GR_RELAX_STRIPS 4  // 32-edge strips a warp relaxes per round
 #endif
 #ifndef GR_BULK_STRIPS
-#define GR_BULK_STRIPS 2  // 32-edge strips a warp relaxes per round in bulk steps
+#define GR_BULK_STRIPS 8   // 32-edge strips a warp relaxes per round in bulk steps
 #endif
+
 // Bulk steps (fire-and-forget atomics and a label-change bitmap, then one
 // pass over the bitmap builds the next piles) pay one extra barrier and a
 // pass over n bits, so by default they start at n / GR_BULK_DIVISOR near rows
