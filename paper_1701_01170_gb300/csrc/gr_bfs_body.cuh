@@ -228,13 +228,20 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
       auto find_parent = [&](bool cand, int beg, int deg) -> int32_t {
         int32_t found = -1;
         const int p = cand ? min(deg, GR_PULL_SERIAL) : 0;
-        for (int e = beg; e < beg + p; ++e) {
-          ++cnt.edges;
-          const int32_t u = __ldg(a.C + e);
-          if ((fcur[u >> 5] >> (u & 31)) & 1u) {
-            found = u;
-            break;
+        // four neighbours per round: their column and bitmap loads overlap
+        for (int e = beg; e < beg + p && found < 0; e += 4) {
+          int32_t u[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            u[j] = e + j < beg + p ? __ldg(a.C + e + j) : -1;
+            if (u[j] >= 0) ++cnt.edges;
           }
+          bool in[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) in[j] = u[j] >= 0 && ((fcur[u[j] >> 5] >> (u[j] & 31)) & 1u);
+#pragma unroll
+          for (int j = 3; j >= 0; --j)
+            if (in[j]) found = u[j];  // the first frontier neighbour in row order
         }
         unsigned pending = __ballot_sync(GR_FULL_MASK, cand && found < 0 && deg > GR_PULL_SERIAL);
         while (pending) {

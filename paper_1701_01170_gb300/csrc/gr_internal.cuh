@@ -250,7 +250,9 @@ __device__ __forceinline__ int gr_next_batch(int cur, int total, int static_span
 }
 
 #define GR_PULL_WORDS 4
+#ifndef GR_PULL_SERIAL
 #define GR_PULL_SERIAL 64  // neighbours a pull candidate scans alone before the warp helps
+#endif
 #define GR_DIRECT_CLAIM_FRONTIER 32768  // below this frontier size BFS claims without a pre-read
 
 // Thread scopes for the query bodies (gr_bfs_body / gr_sssp_body).
