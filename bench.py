@@ -456,29 +456,34 @@ def run_e2e(gr, g, srcs, args, dev, rank):
     outs_d = [torch.empty(n, dtype=torch.int32, device=dev) for _ in range(4)]
     deg = g.degrees()
     stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
 
     def one(src):
+        ev[0].record(stream)
         G.R.copy_(hR, non_blocking=True)
         G.C.copy_(hC, non_blocking=True)
         G.W.copy_(hW, non_blocking=True)
+        ev[1].record(stream)
         gr.gr_bfs(G.handle, src, outs_d[0], outs_d[1], stream=stream)
         gr.gr_sssp(G.handle, src, outs_d[2], outs_d[3], stream=stream)
+        ev[2].record(stream)
         for h, d in zip(outs_h, outs_d):
             h.copy_(d, non_blocking=True)
+        ev[3].record(stream)
 
     k = rank_source_offset(rank)
     one(srcs[0])
     torch.cuda.synchronize()
     ms, edges = 0.0, 0
+    parts = [0.0, 0.0, 0.0]
     for _ in range(args.e2e_steps):
         src = srcs[k % len(srcs)]
         k += 1
-        e0.record(stream)
         one(src)
-        e1.record(stream)
-        e1.synchronize()
-        ms += e0.elapsed_time(e1)
+        ev[3].synchronize()
+        ms += ev[0].elapsed_time(ev[3])
+        for i in range(3):
+            parts[i] += ev[i].elapsed_time(ev[i + 1])
         d = outs_h[0].numpy()
         dist = outs_h[2].numpy()
         edges += int(deg[d >= 0].sum()) + int(deg[dist != -1].sum())
@@ -490,6 +495,9 @@ def run_e2e(gr, g, srcs, args, dev, rank):
             "h2d_bytes_per_step": int(g.R.nbytes + g.C.nbytes + g.W.nbytes),
             "d2h_bytes_per_step": int(4 * n * 4), "steps": args.e2e_steps,
             "ms_per_step": ms / args.e2e_steps,
+            "h2d_ms_per_step": parts[0] / args.e2e_steps,
+            "compute_ms_per_step": parts[1] / args.e2e_steps,
+            "d2h_ms_per_step": parts[2] / args.e2e_steps,
             "note": "CSR re-uploaded from pinned host memory and all four result arrays "
                     "read back every step"}
 

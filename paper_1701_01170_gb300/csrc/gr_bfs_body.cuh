@@ -97,8 +97,10 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
   __shared__ int s_bcnt, s_btot[2];
   GrBigStage bstage{ar.bv, ar.bb, ar.bd, ar.bo, &s_bcnt, s_btot};
   __shared__ unsigned long long s_mfsum;
+  __shared__ int s_found;
   int list_ready = 0;  // the previous level was a pull level that wrote an unvisited list
   int pull = 0;
+  int prev_pull = 0;   // the previous level was a pull level: its frontier exists as a bitmap only
   int L = 0;
   for (;; ++L) {
     const int s0 = L % 3, s1 = (L + 1) % 3, s2 = (L + 2) % 3;
@@ -112,10 +114,13 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
       ustage.reset();
       bstage.reset();
       s_mfsum = 0ull;
+      s_found = 0;
     }
     __syncthreads();
-    const int nq = min(s_nq, a.n);
-    const int nch = (int)min((int64_t)s_nch, a.chunk_cap);
+    // after a pull level qlen counts the discovered vertices without
+    // listing them (the level's frontier is its bitmap)
+    int nq = min(s_nq, a.n);
+    int nch = (int)min((int64_t)s_nch, a.chunk_cap);
     if (nq + nch == 0 || L > a.n) break;
     const int nf = nq + s_nbig;
     const unsigned long long mf = s_mf;
@@ -145,10 +150,55 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
       ctl->mf[s2] = 0ull;
       ctl->work[s2] = 0;
       ctl->workc[s2] = 0;
+      ctl->workb[s2] = 0;
+      ctl->qbuilt[s2] = 0;
       ctl->ulen[s2] = 0;
     }
     if (a.use_do)
       for (int64_t w = gtid; w < a.nwords; w += gthreads) a.front[s2][w] = 0u;
+
+    if (!pull && prev_pull) {
+      // A push level after a pull level: list the frontier from its bitmap
+      // (front[s0]); split rows go to the chunk list as usual.  One pass over
+      // n bits and one barrier, only on pull -> push switches.
+      const uint32_t* fb = a.front[s0];
+      int32_t* qc = a.q[L & 1];
+      int2* chc = a.ch[L & 1];
+      for (int wb = swarp * 32; wb < a.nwords;
+           wb = gr_next_batch(wb, a.nwords, (int)nwarps * 32, &ctl->workb[s0], 32, lane)) {
+        const int w = wb + lane;
+        const uint32_t word = w < a.nwords ? __ldcg(fb + w) : 0u;
+        unsigned nz = __ballot_sync(GR_FULL_MASK, word != 0u);
+        while (nz) {
+          const int j = __ffs(nz) - 1;
+          nz &= nz - 1u;
+          const uint32_t bits = __shfl_sync(GR_FULL_MASK, word, j);
+          const bool mine = (bits >> lane) & 1u;
+          const int32_t v = (wb + j) * 32 + lane;
+          int vb = 0, vd = 0;
+          if (mine) {
+            vb = __ldg(a.R + v);
+            vd = __ldg(a.R + v + 1) - vb;
+          }
+          const bool big = mine && vd >= a.big;
+          stage.append(qc, &ctl->qbuilt[s0], a.n, mine && !big, v, lane);
+          if (big)
+            bstage.add(chc, a.chunk_cap, &ctl->nchunk[s0], &ctl->nbig[s0], v, vb, vd, a.status);
+        }
+      }
+      stage.flush(qc, &ctl->qbuilt[s0], a.n);
+      bstage.flush(chc, a.chunk_cap, &ctl->nchunk[s0], &ctl->nbig[s0], a.status);
+      if (!sc.sync()) return;
+      if (threadIdx.x == 0) {
+        s_nq = __ldcg(&ctl->qbuilt[s0]);
+        s_nch = __ldcg(&ctl->nchunk[s0]);
+        stage.reset();
+        bstage.reset();
+      }
+      __syncthreads();
+      nq = min(s_nq, a.n);
+      nch = (int)min((int64_t)s_nch, a.chunk_cap);
+    }
 
     int32_t* qn = a.q[(L + 1) & 1];
     int2* chn = a.ch[(L + 1) & 1];
@@ -266,18 +316,18 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
         return found;
       };
       // record one candidate's outcome; all 32 lanes
+      // (the next frontier is the bitmap fnext; discoveries are only counted,
+      // and listed by the next level if it is a push level)
       auto commit = [&](bool valid, int32_t v, int32_t found, int beg, int deg) {
+        (void)beg;
         if (found >= 0) {
           ++cnt.updates;
           a.depth[v] = next_depth;
           if (a.pred) a.pred[v] = found;
           my_mf += (unsigned long long)deg;
         }
-        const bool big = found >= 0 && deg >= a.big;
-        stage.append(qn, &ctl->qlen[s1], a.n, found >= 0 && !big, v, lane);
-        if (big)
-          bstage.add(chn, a.chunk_cap, &ctl->nchunk[s1], &ctl->nbig[s1], v, beg, deg,
-                     a.status);
+        const unsigned fm = __ballot_sync(GR_FULL_MASK, found >= 0);
+        if (lane == 0 && fm) atomicAdd(&s_found, __popc(fm));
         // a vertex that can still be discovered stays on the unvisited list
         if (unext) ustage.append(unext, &ctl->ulen[s1], a.n, valid && found < 0 && deg > 0, v, lane);
       };
@@ -374,11 +424,13 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
     stage.flush(qn, &ctl->qlen[s1], a.n);
     if (pull && a.ulist[0]) ustage.flush(a.ulist[(L + 1) & 1], &ctl->ulen[s1], a.n);
     list_ready = pull && a.ulist[0] != nullptr;
+    prev_pull = pull;
     bstage.flush(chn, a.chunk_cap, &ctl->nchunk[s1], &ctl->nbig[s1], a.status);
     my_mf = gr_warp_sum_u64(my_mf);
     if (lane == 0 && my_mf) atomicAdd(&s_mfsum, my_mf);
     __syncthreads();
     if (threadIdx.x == 0 && s_mfsum) atomicAdd(&ctl->mf[s1], s_mfsum);
+    if (threadIdx.x == 0 && s_found) atomicAdd(&ctl->qlen[s1], s_found);
     if (!sc.sync()) return;
   }
   cnt.flush(ctl);

@@ -62,7 +62,8 @@ struct GrCtl {
   int work[3];                     // dynamic work counter (queue batches / pull words)
   int workc[3];                    // dynamic work counter (edge chunks)
   int ulen[3];                     // BFS unvisited-list length, slot = level % 3
-  int workb[3];                    // dynamic work counter (SSSP label-change bitmap words)
+  int workb[3];                    // dynamic work counter (bitmap words: SSSP collect, BFS rebuild)
+  int qbuilt[3];                   // BFS: queue rows rebuilt from a pull level's bitmap
   unsigned farmin[3];              // SSSP smallest distance pushed to a far pile
   int ovf_pending;                 // SSSP: some relaxation sum did not fit in 32 bits
   unsigned long long mf[3];        // sum of degrees of the next frontier
