@@ -452,40 +452,47 @@ def run_e2e(gr, g, srcs, args, dev, rank):
     hC = torch.from_numpy(g.C).pin_memory()
     hW = torch.from_numpy(g.W.view(np.int32)).pin_memory()
     G = gr.Graph.from_csr(g)
-    outs_h = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in range(4)]
+    steps = args.e2e_steps
+    # one set of pinned result buffers per step, so that nothing runs on the
+    # host between the steps; the results are checked after the loop
+    outs_h = [[torch.empty(n, dtype=torch.int32).pin_memory() for _ in range(4)]
+              for _ in range(steps + 1)]
     outs_d = [torch.empty(n, dtype=torch.int32, device=dev) for _ in range(4)]
     deg = g.degrees()
     stream = torch.cuda.current_stream()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps + 1)]
 
-    def one(src):
-        ev[0].record(stream)
+    def one(src, i):
+        ev[i][0].record(stream)
         G.R.copy_(hR, non_blocking=True)
         G.C.copy_(hC, non_blocking=True)
         G.W.copy_(hW, non_blocking=True)
-        ev[1].record(stream)
+        ev[i][1].record(stream)
         gr.gr_bfs(G.handle, src, outs_d[0], outs_d[1], stream=stream)
         gr.gr_sssp(G.handle, src, outs_d[2], outs_d[3], stream=stream)
-        ev[2].record(stream)
-        for h, d in zip(outs_h, outs_d):
+        ev[i][2].record(stream)
+        for h, d in zip(outs_h[i], outs_d):
             h.copy_(d, non_blocking=True)
-        ev[3].record(stream)
+        ev[i][3].record(stream)
 
     k = rank_source_offset(rank)
-    one(srcs[0])
+    one(srcs[0], steps)
+    torch.cuda.synchronize()
+    used = []
+    for i in range(steps):
+        src = srcs[k % len(srcs)]
+        k += 1
+        used.append(src)
+        one(src, i)
     torch.cuda.synchronize()
     ms, edges = 0.0, 0
     parts = [0.0, 0.0, 0.0]
-    for _ in range(args.e2e_steps):
-        src = srcs[k % len(srcs)]
-        k += 1
-        one(src)
-        ev[3].synchronize()
-        ms += ev[0].elapsed_time(ev[3])
-        for i in range(3):
-            parts[i] += ev[i].elapsed_time(ev[i + 1])
-        d = outs_h[0].numpy()
-        dist = outs_h[2].numpy()
+    for i in range(steps):
+        ms += ev[i][0].elapsed_time(ev[i][3])
+        for j in range(3):
+            parts[j] += ev[i][j].elapsed_time(ev[i][j + 1])
+        d = outs_h[i][0].numpy()
+        dist = outs_h[i][2].numpy()
         edges += int(deg[d >= 0].sum()) + int(deg[dist != -1].sum())
     st = G.sync_status()
     G.close()

@@ -149,7 +149,7 @@ static int64_t chunk_capacity(const gr_graph* g, int big) {
 static size_t ws_bytes(const gr_graph* g, int32_t ops) {
   size_t n = (size_t)g->n + 1, bw = bitmap_words(g->n);
   size_t b = sizeof(GrCtl) + 2 * sizeof(int);
-  b += 4 * n * sizeof(int32_t);                                  // queues, unvisited lists
+  b += 6 * n * sizeof(int32_t);                                  // queues, unvisited lists
   b += 2 * (size_t)chunk_capacity(g, 32) * sizeof(int2);         // chunks (smallest big)
   b += 4 * bw * sizeof(uint32_t);                                // visited + 3 frontiers
   b += n * sizeof(int32_t) + bw * sizeof(uint32_t);              // filter scratch
@@ -162,7 +162,8 @@ static size_t ws_bytes(const gr_graph* g, int32_t ops) {
 
 static void ws_free(gr_workspace* ws) {
   if (!ws) return;
-  void* ptrs[] = {ws->ctl, ws->status, ws->q[0], ws->q[1], ws->ulist[0], ws->ulist[1],
+  void* ptrs[] = {ws->ctl, ws->status, ws->q[0], ws->q[1], ws->qm[0], ws->qm[1],
+                  ws->ulist[0], ws->ulist[1],
                   ws->chunks[0], ws->chunks[1],
                   ws->visited, ws->front[0], ws->front[1], ws->front[2], ws->key,
                   ws->far[0], ws->far[1], ws->stamp_near, ws->stamp_far, ws->first_idx,
@@ -198,6 +199,8 @@ static gr_status ws_create(const gr_graph* g, int32_t ops, gr_workspace** out) {
   ALLOC(ws->status, sizeof(int));
   ALLOC(ws->q[0], n * sizeof(int32_t));
   ALLOC(ws->q[1], n * sizeof(int32_t));
+  ALLOC(ws->qm[0], n * sizeof(int32_t));
+  ALLOC(ws->qm[1], n * sizeof(int32_t));
   ALLOC(ws->ulist[0], n * sizeof(int32_t));
   ALLOC(ws->ulist[1], n * sizeof(int32_t));
   ALLOC(ws->chunks[0], ws->chunk_cap * sizeof(int2));

@@ -54,8 +54,8 @@ struct BatchArgs {
 
 // slot layout (byte offsets, 256-aligned)
 struct SlotLayout {
-  size_t ctl, job, q0, q1, ul0, ul1, ch0, ch1, vis, fr0, fr1, fr2, key, far0, far1, stn, stf,
-      total;
+  size_t ctl, job, q0, q1, qm0, qm1, ul0, ul1, ch0, ch1, vis, fr0, fr1, fr2, key, far0, far1,
+      stn, stf, total;
 };
 
 size_t r256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -71,6 +71,8 @@ SlotLayout slot_layout(int32_t nmax, int64_t chunk_cap) {
   L.job = o; o += 256;
   L.q0 = o; o += nq;
   L.q1 = o; o += nq;
+  L.qm0 = o; o += nq;
+  L.qm1 = o; o += nq;
   L.ul0 = o; o += nq;
   L.ul1 = o; o += nq;
   L.ch0 = o; o += nc;
@@ -139,6 +141,8 @@ __global__ void __launch_bounds__(BT) batch_kernel(BatchArgs b, SlotLayout L) {
       a.front[2] = (uint32_t*)(base + L.fr2);
       a.q[0] = (int32_t*)(base + L.q0);
       a.q[1] = (int32_t*)(base + L.q1);
+      a.qm[0] = (int32_t*)(base + L.qm0);
+      a.qm[1] = (int32_t*)(base + L.qm1);
       a.ulist[0] = (int32_t*)(base + L.ul0);
       a.ulist[1] = (int32_t*)(base + L.ul1);
       a.ch[0] = (int2*)(base + L.ch0);
@@ -151,7 +155,7 @@ __global__ void __launch_bounds__(BT) batch_kernel(BatchArgs b, SlotLayout L) {
       a.use_do = (J.flags & GR_SYMMETRIC) ? 1 : 0;
       a.force_pull = 0;
       a.big = J.big;
-      a.track_deg = a.use_do || J.max_degree >= J.big;
+      a.track_deg = a.use_do || J.max_degree >= GR_MEDIUM_DEGREE;
       a.do_a = J.do_a;
       a.do_b = J.do_b;
       a.spin = b.spin;
@@ -167,6 +171,8 @@ __global__ void __launch_bounds__(BT) batch_kernel(BatchArgs b, SlotLayout L) {
       a.pred = J.pred;
       a.q[0] = (int32_t*)(base + L.q0);
       a.q[1] = (int32_t*)(base + L.q1);
+      a.qm[0] = (int32_t*)(base + L.qm0);
+      a.qm[1] = (int32_t*)(base + L.qm1);
       a.ch[0] = (int2*)(base + L.ch0);
       a.ch[1] = (int2*)(base + L.ch1);
       a.chunk_cap = b.chunk_cap;
@@ -181,7 +187,7 @@ __global__ void __launch_bounds__(BT) batch_kernel(BatchArgs b, SlotLayout L) {
       a.src = J.src;
       a.delta = J.delta;
       a.big = J.big;
-      a.track_deg = J.max_degree >= J.big;
+      a.track_deg = J.max_degree >= GR_MEDIUM_DEGREE;
       a.spin = b.spin;
       gr_sssp_body(a, sc, ar);
     }

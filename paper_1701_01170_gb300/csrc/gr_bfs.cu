@@ -77,6 +77,8 @@ extern "C" gr_status gr_bfs(const gr_graph* g, int32_t src, int32_t* depth, int3
   for (int i = 0; i < 3; ++i) a.front[i] = ws->front[i];
   a.q[0] = ws->q[0];
   a.q[1] = ws->q[1];
+  a.qm[0] = ws->qm[0];
+  a.qm[1] = ws->qm[1];
   a.ulist[0] = ws->ulist[0];
   a.ulist[1] = ws->ulist[1];
   a.ch[0] = ws->chunks[0];
@@ -89,7 +91,7 @@ extern "C" gr_status gr_bfs(const gr_graph* g, int32_t src, int32_t* depth, int3
   a.use_do = symmetric && o.direction != GR_DIR_PUSH;
   a.force_pull = o.direction == GR_DIR_PULL;
   a.big = o.big_degree > 0 ? (o.big_degree < 32 ? 32 : o.big_degree) : GR_DEFAULT_BIG_DEGREE;
-  a.track_deg = a.use_do || g->max_degree >= a.big;
+  a.track_deg = a.use_do || g->max_degree >= GR_MEDIUM_DEGREE;
   a.do_a = o.do_a;
   a.do_b = o.do_b;
   a.spin = o.spin_limit ? o.spin_limit : GR_DEFAULT_SPIN_LIMIT;

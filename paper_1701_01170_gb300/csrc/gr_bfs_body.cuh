@@ -22,6 +22,7 @@ struct BfsArgs {
   uint32_t* visited;
   uint32_t* front[3];
   int32_t* q[2];
+  int32_t* qm[2];     // medium-row queues (NULL: medium rows go to q)
   int32_t* ulist[2];  // unvisited lists of pull levels (NULL: rescan the bitmap every level)
   int2* ch[2];
   int64_t chunk_cap;
@@ -89,10 +90,12 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
   GrCounters cnt;
   // step counters are read once per CTA and broadcast through shared memory
   // (one L2 request per CTA instead of one per warp)
-  __shared__ int s_nq, s_nch, s_nbig;
+  __shared__ int s_nq, s_nqm, s_nch, s_nbig;
   __shared__ unsigned long long s_mf;
   __shared__ int s_qcnt, s_qbase, s_ucnt, s_ubase, s_nu;
   GrStage stage{ar.buf0, &s_qcnt, &s_qbase};
+  __shared__ int s_mcnt, s_mbase;
+  GrStage mstage{ar.bufm, &s_mcnt, &s_mbase};
   GrStage ustage{ar.buf1, &s_ucnt, &s_ubase};
   __shared__ int s_bcnt, s_btot[2];
   GrBigStage bstage{ar.bv, ar.bb, ar.bd, ar.bo, &s_bcnt, s_btot};
@@ -106,11 +109,13 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
     const int s0 = L % 3, s1 = (L + 1) % 3, s2 = (L + 2) % 3;
     if (threadIdx.x == 0) {
       s_nq = __ldcg(&ctl->qlen[s0]);
+      s_nqm = __ldcg(&ctl->qmlen[s0]);
       s_nch = __ldcg(&ctl->nchunk[s0]);
       s_nbig = __ldcg(&ctl->nbig[s0]);
       s_mf = __ldcg(&ctl->mf[s0]);
       s_nu = __ldcg(&ctl->ulen[s0]);
       stage.reset();
+      mstage.reset();
       ustage.reset();
       bstage.reset();
       s_mfsum = 0ull;
@@ -120,9 +125,10 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
     // after a pull level qlen counts the discovered vertices without
     // listing them (the level's frontier is its bitmap)
     int nq = min(s_nq, a.n);
+    int nqm = min(s_nqm, a.n);
     int nch = (int)min((int64_t)s_nch, a.chunk_cap);
-    if (nq + nch == 0 || L > a.n) break;
-    const int nf = nq + s_nbig;
+    if (nq + nqm + nch == 0 || L > a.n) break;
+    const int nf = nq + nqm + s_nbig;
     const unsigned long long mf = s_mf;
     seen_edges += mf;
     const unsigned long long mu = (unsigned long long)a.m > seen_edges
@@ -145,6 +151,8 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
             (int)min(gr_globaltimer() - (deadline - GR_TIME_LIMIT_NS), (unsigned long long)INT_MAX);
       }
       ctl->qlen[s2] = 0;
+      ctl->qmlen[s2] = 0;
+      ctl->workm[s2] = 0;
       ctl->nchunk[s2] = 0;
       ctl->nbig[s2] = 0;
       ctl->mf[s2] = 0ull;
@@ -163,6 +171,7 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
       // n bits and one barrier, only on pull -> push switches.
       const uint32_t* fb = a.front[s0];
       int32_t* qc = a.q[L & 1];
+      int32_t* qmc = a.qm[0] ? a.qm[L & 1] : nullptr;
       int2* chc = a.ch[L & 1];
       for (int wb = swarp * 32; wb < a.nwords;
            wb = gr_next_batch(wb, a.nwords, (int)nwarps * 32, &ctl->workb[s0], 32, lane)) {
@@ -181,26 +190,33 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
             vd = __ldg(a.R + v + 1) - vb;
           }
           const bool big = mine && vd >= a.big;
-          stage.append(qc, &ctl->qbuilt[s0], a.n, mine && !big, v, lane);
+          const bool mid = mine && !big && qmc && vd >= GR_MEDIUM_DEGREE;
+          stage.append(qc, &ctl->qbuilt[s0], a.n, mine && !big && !mid, v, lane);
+          mstage.append(qmc, &ctl->qmlen[s0], a.n, mid, v, lane);
           if (big)
             bstage.add(chc, a.chunk_cap, &ctl->nchunk[s0], &ctl->nbig[s0], v, vb, vd, a.status);
         }
       }
       stage.flush(qc, &ctl->qbuilt[s0], a.n);
+      mstage.flush(qmc, &ctl->qmlen[s0], a.n);
       bstage.flush(chc, a.chunk_cap, &ctl->nchunk[s0], &ctl->nbig[s0], a.status);
       if (!sc.sync()) return;
       if (threadIdx.x == 0) {
         s_nq = __ldcg(&ctl->qbuilt[s0]);
+        s_nqm = __ldcg(&ctl->qmlen[s0]);
         s_nch = __ldcg(&ctl->nchunk[s0]);
         stage.reset();
+        mstage.reset();
         bstage.reset();
       }
       __syncthreads();
       nq = min(s_nq, a.n);
+      nqm = min(s_nqm, a.n);
       nch = (int)min((int64_t)s_nch, a.chunk_cap);
     }
 
     int32_t* qn = a.q[(L + 1) & 1];
+    int32_t* qmn = a.qm[0] ? a.qm[(L + 1) & 1] : nullptr;
     int2* chn = a.ch[(L + 1) & 1];
     uint32_t* fnext = a.front[s1];
     unsigned long long my_mf = 0;
@@ -214,7 +230,9 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
       // a large frontier mostly meets visited vertices: test with a plain load
       // before claiming; a small one (mesh-like graphs) claims directly and
       // saves a dependent round trip per level
-      const bool direct_claim = nf < GR_DIRECT_CLAIM_FRONTIER;
+      // (a few rows with many edges count as large: their targets repeat)
+      const bool direct_claim =
+          nf < GR_DIRECT_CLAIM_FRONTIER && (!a.track_deg || mf < 2ull * GR_DIRECT_CLAIM_FRONTIER);
       // pass 2 of the multi-strip expansion: the visited word of each target
       auto pre = [&](bool active, int, int32_t v) -> uint32_t {
         return (active && !direct_claim) ? a.visited[v >> 5] : 0u;
@@ -236,34 +254,24 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
           }
         }
         const bool big = won && vdeg >= a.big;
-        stage.append(qn, &ctl->qlen[s1], a.n, won && !big, v, lane);
+        const bool mid = won && !big && qmn && vdeg >= GR_MEDIUM_DEGREE;
+        stage.append(qn, &ctl->qlen[s1], a.n, won && !big && !mid, v, lane);
+        mstage.append(qmn, &ctl->qmlen[s1], a.n, mid, v, lane);
         if (big)
           bstage.add(chn, a.chunk_cap, &ctl->nchunk[s1], &ctl->nbig[s1], v, vbeg, vdeg,
                      a.status);
       };
-      // warps take 32 frontier rows at a time: the first batch by warp index,
-      // further batches from a counter (idle warps never touch it)
-      for (int base = swarp * 32; base < nq;
-           base = gr_next_batch(base, nq, (int)nwarps * 32, &ctl->work[s0], 32, lane)) {
-        const int i = base + lane;
-        const bool valid = i < nq;
-        int32_t u = 0;
-        int beg = 0, deg = 0;
-        if (valid) {
-          ++cnt.verts;
-          u = __ldcg(q + i);
-          beg = __ldg(a.R + u);
-          deg = __ldg(a.R + u + 1) - beg;
-        }
-        gr_warp_expand_u<GR_VISIT_STRIPS>(a.R, a.C, valid, u, beg, deg, 0u, lane, pre, visit);
-      }
-      // then one 1024-edge chunk of a long row at a time
-      for (int c = swarp; c < nch; c = gr_next_batch(c, nch, (int)nwarps, &ctl->workc[s0], 1, lane)) {
-        const int2 cu = __ldcg(ch + c);
-        const int e1 = min(cu.y + GR_CHUNK_EDGES, __ldg(a.R + cu.x + 1));
-        if (lane == 0) ++cnt.verts;
-        gr_warp_chunk_u<GR_VISIT_STRIPS>(a.C, cu.x, cu.y, e1, 0u, lane, pre, visit);
-      }
+      // largest work first: edge chunks of split rows, then medium rows,
+      // then short rows 32 at a time (first batch by warp index, further
+      // batches from a counter that idle warps never touch)
+      auto no_payload = [](int32_t) -> uint32_t { return 0u; };
+      gr_chunks_loop<GR_VISIT_STRIPS>(ch, nch, &ctl->workc[s0], swarp, (int)nwarps, lane, a.R, a.C,
+                                      cnt, no_payload, pre, visit);
+      if (a.qm[0])
+        gr_rows_loop<GR_VISIT_STRIPS>(a.qm[L & 1], nqm, GR_MEDIUM_BATCH, &ctl->workm[s0], swarp,
+                                      (int)nwarps, lane, a.R, a.C, cnt, no_payload, pre, visit);
+      gr_rows_loop<GR_VISIT_STRIPS>(q, nq, 32, &ctl->work[s0], swarp, (int)nwarps, lane, a.R, a.C,
+                                    cnt, no_payload, pre, visit);
     } else {
       // ---- pull: unvisited vertices look for a parent in the frontier ----
       // (Alg. 2 Reverse_Advance: the step yields the next active frontier and
@@ -422,6 +430,7 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
       }
     }
     stage.flush(qn, &ctl->qlen[s1], a.n);
+    mstage.flush(qmn, &ctl->qmlen[s1], a.n);
     if (pull && a.ulist[0]) ustage.flush(a.ulist[(L + 1) & 1], &ctl->ulen[s1], a.n);
     list_ready = pull && a.ulist[0] != nullptr;
     prev_pull = pull;

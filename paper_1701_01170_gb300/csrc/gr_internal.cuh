@@ -64,6 +64,8 @@ struct GrCtl {
   int ulen[3];                     // BFS unvisited-list length, slot = level % 3
   int workb[3];                    // dynamic work counter (bitmap words: SSSP collect, BFS rebuild)
   int qbuilt[3];                   // BFS: queue rows rebuilt from a pull level's bitmap
+  int qmlen[3];                    // medium-row queue length, slot = step % 3
+  int workm[3];                    // dynamic work counter (medium-row batches)
   unsigned farmin[3];              // SSSP smallest distance pushed to a far pile
   int ovf_pending;                 // SSSP: some relaxation sum did not fit in 32 bits
   unsigned long long mf[3];        // sum of degrees of the next frontier
@@ -129,6 +131,7 @@ struct gr_workspace {
   int* status;
   int* h_status;        // pinned host mirror used by gr_sync_status
   int32_t* q[2];        // frontier queues (ping-pong), n entries each
+  int32_t* qm[2];       // medium-row frontier queues (ping-pong), n entries each
   int32_t* ulist[2];    // BFS unvisited lists (ping-pong), n entries each
   int2* chunks[2];      // (row, first edge) chunks of split rows (ping-pong)
   int64_t chunk_cap;
@@ -251,10 +254,18 @@ __device__ __forceinline__ int gr_next_batch(int cur, int total, int static_span
 }
 
 #define GR_PULL_WORDS 4
+// Rows are expanded in three classes (the paper's TWC classes, Sec. 5.1.2):
+// rows shorter than GR_MEDIUM_DEGREE in batches of 32 per warp, medium rows
+// in batches of GR_MEDIUM_BATCH per warp, rows of at least the split
+// threshold as GR_CHUNK_EDGES-edge chunks shared by the grid.  A batch then
+// holds at most 32 * 31 or GR_MEDIUM_BATCH * (split threshold) edges.
+#define GR_MEDIUM_DEGREE 32
+#define GR_MEDIUM_BATCH 4
 #ifndef GR_PULL_SERIAL
 #define GR_PULL_SERIAL 64  // neighbours a pull candidate scans alone before the warp helps
 #endif
-#define GR_DIRECT_CLAIM_FRONTIER 32768  // below this frontier size BFS claims without a pre-read
+#define GR_DIRECT_CLAIM_FRONTIER 32768  // below this frontier size (and twice as many
+                                        // frontier edges) BFS claims without a pre-read
 
 // Thread scopes for the query bodies (gr_bfs_body / gr_sssp_body).
 // GridScope: every thread of a cooperative (co-resident) launch; the step
@@ -494,6 +505,49 @@ __device__ __forceinline__ void gr_warp_chunk_u(const int32_t* __restrict__ C, i
   }
 }
 
+// Static-first / dynamic loop over a row list, `per` rows per warp batch,
+// each batch expanded with gr_warp_expand_u<U>; payload(u) gives the value
+// passed to the edge functor with every edge of row u.
+template <int U, class Payload, class Pre, class Edge>
+__device__ __forceinline__ void gr_rows_loop(const int32_t* list, int len, int per, int* counter,
+                                             int swarp, int nwarps, int lane,
+                                             const int32_t* __restrict__ R,
+                                             const int32_t* __restrict__ C, GrCounters& cnt,
+                                             Payload&& payload, Pre&& pre, Edge&& edge) {
+  for (int base = swarp * per; base < len;
+       base = gr_next_batch(base, len, nwarps * per, counter, per, lane)) {
+    const int i = base + lane;
+    const bool valid = lane < per && i < len;
+    int32_t u = 0;
+    int beg = 0, deg = 0;
+    uint32_t pl = 0;
+    if (valid) {
+      ++cnt.verts;
+      u = __ldcg(list + i);
+      beg = __ldg(R + u);
+      deg = __ldg(R + u + 1) - beg;
+      pl = payload(u);
+    }
+    gr_warp_expand_u<U>(R, C, valid, u, beg, deg, pl, lane, pre, edge);
+  }
+}
+
+// Static-first / dynamic loop over the edge chunks of split rows.
+template <int U, class Payload, class Pre, class Edge>
+__device__ __forceinline__ void gr_chunks_loop(const int2* ch, int nch, int* counter, int swarp,
+                                               int nwarps, int lane,
+                                               const int32_t* __restrict__ R,
+                                               const int32_t* __restrict__ C, GrCounters& cnt,
+                                               Payload&& payload, Pre&& pre, Edge&& edge) {
+  for (int c = swarp; c < nch; c = gr_next_batch(c, nch, nwarps, counter, 1, lane)) {
+    const int2 cu = __ldcg(ch + c);
+    const int e1 = min(cu.y + GR_CHUNK_EDGES, __ldg(R + cu.x + 1));
+    const uint32_t pl = payload(cu.x);
+    if (lane == 0) ++cnt.verts;
+    gr_warp_chunk_u<U>(C, cu.x, cu.y, e1, pl, lane, pre, edge);
+  }
+}
+
 // Default SSSP bucket width: 256 * mean weight / mean degree (at least 1).
 // Wide buckets trade a few repeated relaxations for far fewer grid-wide
 // steps, which is what bounds both low-diameter and mesh-like graphs here.
@@ -594,6 +648,7 @@ struct GrBigStage {
 // holds both bodies but needs only one arena).
 struct GrArena {
   int buf0[GR_STAGE_CAP];  // BFS next frontier / SSSP near frontier
+  int bufm[GR_STAGE_CAP];  // medium rows of the next frontier
   int buf1[GR_STAGE_CAP];  // BFS unvisited list / SSSP far pile
   int bv[GR_BIG_STAGE_CAP], bb[GR_BIG_STAGE_CAP], bd[GR_BIG_STAGE_CAP], bo[GR_BIG_STAGE_CAP];
 };

@@ -77,6 +77,8 @@ extern "C" gr_status gr_sssp(const gr_graph* g, int32_t src, uint32_t* dist, int
   a.pred = pred;
   a.q[0] = ws->q[0];
   a.q[1] = ws->q[1];
+  a.qm[0] = ws->qm[0];
+  a.qm[1] = ws->qm[1];
   a.ch[0] = ws->chunks[0];
   a.ch[1] = ws->chunks[1];
   a.chunk_cap = ws->chunk_cap;
@@ -91,7 +93,7 @@ extern "C" gr_status gr_sssp(const gr_graph* g, int32_t src, uint32_t* dist, int
   a.src = src;
   a.delta = o.delta ? o.delta : default_delta(g);
   a.big = o.big_degree > 0 ? (o.big_degree < 32 ? 32 : o.big_degree) : GR_DEFAULT_BIG_DEGREE;
-  a.track_deg = g->max_degree >= a.big;
+  a.track_deg = g->max_degree >= GR_MEDIUM_DEGREE;
   a.spin = o.spin_limit ? o.spin_limit : GR_DEFAULT_SPIN_LIMIT;
   a.level_stats = o.level_stats;
   a.max_levels = o.max_levels;

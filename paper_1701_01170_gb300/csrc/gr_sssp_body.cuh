@@ -35,6 +35,7 @@ struct SsspArgs {
   uint32_t* dist;
   int32_t* pred;
   int32_t* q[2];
+  int32_t* qm[2];     // medium-row queues (NULL: medium rows go to q)
   int2* ch[2];
   int64_t chunk_cap;
   int32_t* far[2];
@@ -97,11 +98,13 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
   GrCounters cnt;
   bool ovf_seen = false;
   // step counters are read once per CTA and broadcast through shared memory
-  __shared__ int s_nq, s_nch, s_nbig, s_flen;
+  __shared__ int s_nq, s_nqm, s_nch, s_nbig, s_flen;
   __shared__ unsigned s_fm;
   __shared__ int s_ncnt, s_nbase, s_fcnt, s_fbase;
   __shared__ unsigned s_farmin;
   GrStage near_stage{ar.buf0, &s_ncnt, &s_nbase};
+  __shared__ int s_mcnt, s_mbase;
+  GrStage mid_stage{ar.bufm, &s_mcnt, &s_mbase};
   GrStage far_stage{ar.buf1, &s_fcnt, &s_fbase};
   __shared__ int s_bcnt, s_btot[2];
   GrBigStage bstage{ar.bv, ar.bb, ar.bd, ar.bo, &s_bcnt, s_btot};
@@ -110,32 +113,38 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
     const int fs = fe % 3;
     if (threadIdx.x == 0) {
       s_nq = __ldcg(&ctl->qlen[s0]);
+      s_nqm = __ldcg(&ctl->qmlen[s0]);
       s_nch = __ldcg(&ctl->nchunk[s0]);
       s_nbig = __ldcg(&ctl->nbig[s0]);
       s_flen = __ldcg(&ctl->farlen[fs]);
       s_fm = __ldcg(&ctl->farmin[fs]);
       near_stage.reset();
+      mid_stage.reset();
       far_stage.reset();
       bstage.reset();
       s_farmin = UINT_MAX;
     }
     __syncthreads();
     const int nq = min(s_nq, a.n);
+    const int nqm = min(s_nqm, a.n);
     const int nch = (int)min((int64_t)s_nch, a.chunk_cap);
+    const int nrows = nq + nqm + nch;  // zero: a SPLIT step
     const int flen = min(s_flen, a.n);
     const unsigned fm_step = s_fm;
-    if (nq + nch == 0 && flen == 0) break;
+    if (nrows == 0 && flen == 0) break;
     if (gtid == 0) {
       if ((it & 63) == 0) gr_check_deadline(ctl, a.status, deadline);
       if (a.level_stats && it < a.max_levels) {
-        a.level_stats[4 * it] = nq + s_nbig;
-        a.level_stats[4 * it + 1] = nq + nch == 0;
+        a.level_stats[4 * it] = nq + nqm + s_nbig;
+        a.level_stats[4 * it + 1] = nrows == 0;
         a.level_stats[4 * it + 2] = flen;
         // start of this step in ns after the first step started
         a.level_stats[4 * it + 3] =
             (int)min(gr_globaltimer() - (deadline - GR_TIME_LIMIT_NS), (unsigned long long)INT_MAX);
       }
       ctl->qlen[s2] = 0;
+      ctl->qmlen[s2] = 0;
+      ctl->workm[s2] = 0;
       ctl->nchunk[s2] = 0;
       ctl->nbig[s2] = 0;
       ctl->work[s2] = 0;
@@ -143,6 +152,7 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
       ctl->workb[s2] = 0;
     }
     int32_t* qn = a.q[(it + 1) & 1];
+    int32_t* qmn = a.qm[0] ? a.qm[(it + 1) & 1] : nullptr;
     int2* chn = a.ch[(it + 1) & 1];
     const int next_stamp = it + 1;
 
@@ -154,7 +164,9 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
         vdeg = __ldg(a.R + v + 1) - vbeg;
       }
       const bool big = take && vdeg >= a.big;
-      near_stage.append(qn, &ctl->qlen[s1], a.n, take && !big, v, lane);
+      const bool mid = take && !big && qmn && vdeg >= GR_MEDIUM_DEGREE;
+      near_stage.append(qn, &ctl->qlen[s1], a.n, take && !big && !mid, v, lane);
+      mid_stage.append(qmn, &ctl->qmlen[s1], a.n, mid, v, lane);
       if (big)
         bstage.add(chn, a.chunk_cap, &ctl->nchunk[s1], &ctl->nbig[s1], v, vbeg, vdeg, a.status);
     };
@@ -166,7 +178,7 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
     // join far pile `epoch` (once per epoch) — all lanes call this
     // (a step only ever writes one far pile: epoch fe when relaxing, fe + 1
     // when splitting)
-    const int fe_out = nq + nch > 0 ? fe : fe + 1;
+    const int fe_out = nrows > 0 ? fe : fe + 1;
     auto to_far = [&](bool take, int32_t v, unsigned d, int epoch) {
       if (take) take = atomicExch(&a.stamp_far[v], epoch) != epoch;
       far_stage.append(a.far[epoch & 1], &ctl->farlen[epoch % 3], a.n, take, v, lane);
@@ -174,7 +186,7 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
       if (lane == 0 && mn != UINT_MAX) atomicMin(&s_farmin, mn);
     };
 
-    const bool bulk = a.touched && nq + 8ll * nch >= a.bulk_rows;
+    const bool bulk = a.touched && nq + 4ll * nqm + 8ll * nch >= a.bulk_rows;
     if (bulk) {
       // ---- bulk RELAX: Update_Label / Set_Pred as fire-and-forget 64-bit
       // atomicMin, plus one bit per changed label; no return values and no
@@ -214,29 +226,15 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
         }
         if (hit) atomicOr(a.touched + (v >> 5), 1u << (v & 31));
       };
-      for (int base = swarp * 32; base < nq;
-           base = gr_next_batch(base, nq, (int)nwarps * 32, &ctl->work[s0], 32, lane)) {
-        const int i = base + lane;
-        const bool valid = i < nq;
-        int32_t u = 0;
-        int beg = 0, deg = 0;
-        uint32_t du = 0;
-        if (valid) {
-          ++cnt.verts;
-          u = __ldcg(q + i);
-          beg = __ldg(a.R + u);
-          deg = __ldg(a.R + u + 1) - beg;
-          du = (uint32_t)(__ldcg(a.key + u) >> 32);
-        }
-        gr_warp_expand_u<GR_BULK_STRIPS>(a.R, a.C, valid, u, beg, deg, du, lane, pre, relax);
-      }
-      for (int c = swarp; c < nch; c = gr_next_batch(c, nch, (int)nwarps, &ctl->workc[s0], 1, lane)) {
-        const int2 cu = __ldcg(ch + c);
-        const int e1 = min(cu.y + GR_CHUNK_EDGES, __ldg(a.R + cu.x + 1));
-        const uint32_t du = (uint32_t)(__ldcg(a.key + cu.x) >> 32);
-        if (lane == 0) ++cnt.verts;
-        gr_warp_chunk_u<GR_BULK_STRIPS>(a.C, cu.x, cu.y, e1, du, lane, pre, relax);
-      }
+      // largest work first: chunks, medium rows, then short rows
+      auto label = [&](int32_t u) -> uint32_t { return (uint32_t)(__ldcg(a.key + u) >> 32); };
+      gr_chunks_loop<GR_BULK_STRIPS>(ch, nch, &ctl->workc[s0], swarp, (int)nwarps, lane, a.R, a.C,
+                                     cnt, label, pre, relax);
+      if (a.qm[0])
+        gr_rows_loop<GR_BULK_STRIPS>(a.qm[it & 1], nqm, GR_MEDIUM_BATCH, &ctl->workm[s0], swarp,
+                                     (int)nwarps, lane, a.R, a.C, cnt, label, pre, relax);
+      gr_rows_loop<GR_BULK_STRIPS>(q, nq, 32, &ctl->work[s0], swarp, (int)nwarps, lane, a.R, a.C,
+                                   cnt, label, pre, relax);
       if (!sc.sync()) return;
       // ---- collect: every vertex whose label dropped in this step joins
       // the near frontier (dist < T) or, once per epoch, the far pile.  A
@@ -269,7 +267,7 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
           if (lane == 0 && mn != UINT_MAX) atomicMin(&s_farmin, mn);
         }
       }
-    } else if (nq + nch > 0) {
+    } else if (nrows > 0) {
       // ---- RELAX: advance + Update_Label / Set_Pred + Remove_Redundant ----
       const int32_t* q = a.q[it & 1];
       const int2* ch = a.ch[it & 1];
@@ -309,32 +307,17 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
         to_near(imp && nd < T, v);
         to_far(imp && nd >= T, v, (unsigned)nd, fe);
       };
-      // warps take 32 near-frontier rows at a time: the first batch by warp
-      // index, further batches from a counter (idle warps never touch it)
-      for (int base = swarp * 32; base < nq;
-           base = gr_next_batch(base, nq, (int)nwarps * 32, &ctl->work[s0], 32, lane)) {
-        const int i = base + lane;
-        const bool valid = i < nq;
-        int32_t u = 0;
-        int beg = 0, deg = 0;
-        uint32_t du = 0;
-        if (valid) {
-          ++cnt.verts;
-          u = __ldcg(q + i);
-          beg = __ldg(a.R + u);
-          deg = __ldg(a.R + u + 1) - beg;
-          du = (uint32_t)(a.key[u] >> 32);
-        }
-        gr_warp_expand_u<GR_RELAX_STRIPS>(a.R, a.C, valid, u, beg, deg, du, lane, pre, relax);
-      }
-      // then one 1024-edge chunk of a long row at a time
-      for (int c = swarp; c < nch; c = gr_next_batch(c, nch, (int)nwarps, &ctl->workc[s0], 1, lane)) {
-        const int2 cu = __ldcg(ch + c);
-        const int e1 = min(cu.y + GR_CHUNK_EDGES, __ldg(a.R + cu.x + 1));
-        const uint32_t du = (uint32_t)(a.key[cu.x] >> 32);
-        if (lane == 0) ++cnt.verts;
-        gr_warp_chunk_u<GR_RELAX_STRIPS>(a.C, cu.x, cu.y, e1, du, lane, pre, relax);
-      }
+      // largest work first: chunks, medium rows, then short rows 32 at a time
+      // (first batch by warp index, further batches from a counter that idle
+      // warps never touch)
+      auto label = [&](int32_t u) -> uint32_t { return (uint32_t)(a.key[u] >> 32); };
+      gr_chunks_loop<GR_RELAX_STRIPS>(ch, nch, &ctl->workc[s0], swarp, (int)nwarps, lane, a.R, a.C,
+                                      cnt, label, pre, relax);
+      if (a.qm[0])
+        gr_rows_loop<GR_RELAX_STRIPS>(a.qm[it & 1], nqm, GR_MEDIUM_BATCH, &ctl->workm[s0], swarp,
+                                      (int)nwarps, lane, a.R, a.C, cnt, label, pre, relax);
+      gr_rows_loop<GR_RELAX_STRIPS>(q, nq, 32, &ctl->work[s0], swarp, (int)nwarps, lane, a.R, a.C,
+                                    cnt, label, pre, relax);
     } else {
       // ---- SPLIT: raise the threshold, move far entries below it to near --
       const unsigned fm = fm_step;
@@ -367,6 +350,7 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
       ++fe;
     }
     near_stage.flush(qn, &ctl->qlen[s1], a.n);
+    mid_stage.flush(qmn, &ctl->qmlen[s1], a.n);
     bstage.flush(chn, a.chunk_cap, &ctl->nchunk[s1], &ctl->nbig[s1], a.status);
     far_stage.flush(a.far[fe_out & 1], &ctl->farlen[fe_out % 3], a.n);
     if (threadIdx.x == 0 && s_farmin != UINT_MAX) atomicMin(&ctl->farmin[fe_out % 3], s_farmin);
