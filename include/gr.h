@@ -258,7 +258,10 @@ typedef struct gr_bfs_opts {
   float do_a;            /* push -> pull when m_f > m_u * do_a (Eq. 5)          */
   float do_b;            /* pull -> push when m_f < m_u * do_b (Eq. 6)          */
   int32_t big_degree;    /* rows at least this long are split into edge chunks
-                            shared by the whole grid; 0 = library default     */
+                            shared by the whole grid, rows of 32 edges up to
+                            this length are expanded 4 per warp, shorter rows
+                            32 per warp (Sec. 5.1.2 classes); 0 = library
+                            default (256)                                     */
   int32_t blocks_per_sm; /* persistent grid = blocks_per_sm * SMs; 0 = max    */
   uint32_t spin_limit;   /* grid-barrier wait budget in polls; 0 = default    */
   gr_workspace* ws;      /* NULL = the graph's default workspace              */
@@ -284,7 +287,7 @@ gr_status gr_bfs(const gr_graph* g, int32_t src, int32_t* depth, int32_t* pred,
 
 typedef struct gr_sssp_opts {
   uint32_t delta;        /* near/far bucket width; 0 = derived from the graph */
-  int32_t big_degree;    /* as in gr_bfs_opts                                  */
+  int32_t big_degree;    /* as in gr_bfs_opts; 0 = library default (1024)     */
   int32_t blocks_per_sm; /* as in gr_bfs_opts                                  */
   uint32_t spin_limit;   /* as in gr_bfs_opts                                  */
   gr_workspace* ws;      /* NULL = the graph's default workspace              */

@@ -276,7 +276,8 @@ extern "C" gr_status gr_batch_create(const gr_job* jobs, int32_t njobs, const gr
     if (J.op == GR_OP_SSSP && !g->W && g->m > 0) return GR_ERR_UNSUPPORTED;
     if (device < 0) device = g->device;
     if (g->device != device) return GR_ERR_INVALID_ARG;
-    const int big = J.big_degree > 0 ? std::max(J.big_degree, 32) : GR_DEFAULT_BIG_DEGREE;
+    const int big = J.big_degree > 0 ? std::max(J.big_degree, 32)
+                                     : (J.op == GR_OP_BFS ? GR_DEFAULT_BFS_BIG : GR_DEFAULT_SSSP_BIG);
     nmax = std::max(nmax, g->n);
     chunk_cap = std::max<int64_t>(chunk_cap, g->m / GR_CHUNK_EDGES + g->m / big + 2);
     DevJob d = {};

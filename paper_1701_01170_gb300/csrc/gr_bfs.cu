@@ -43,7 +43,7 @@ extern "C" void gr_bfs_opts_default(gr_bfs_opts* o) {
   o->direction = GR_DIR_AUTO;
   o->do_a = 0.05f;
   o->do_b = 0.05f;
-  o->big_degree = GR_DEFAULT_BIG_DEGREE;
+  o->big_degree = GR_DEFAULT_BFS_BIG;
   o->blocks_per_sm = 0;
   o->spin_limit = GR_DEFAULT_SPIN_LIMIT;
   o->ws = nullptr;
@@ -90,7 +90,7 @@ extern "C" gr_status gr_bfs(const gr_graph* g, int32_t src, int32_t* depth, int3
   a.nwords = (int32_t)(((int64_t)g->n + 31) / 32);
   a.use_do = symmetric && o.direction != GR_DIR_PUSH;
   a.force_pull = o.direction == GR_DIR_PULL;
-  a.big = o.big_degree > 0 ? (o.big_degree < 32 ? 32 : o.big_degree) : GR_DEFAULT_BIG_DEGREE;
+  a.big = o.big_degree > 0 ? (o.big_degree < 32 ? 32 : o.big_degree) : GR_DEFAULT_BFS_BIG;
   a.track_deg = a.use_do || g->max_degree >= GR_MEDIUM_DEGREE;
   a.do_a = o.do_a;
   a.do_b = o.do_b;
@@ -137,7 +137,7 @@ namespace {
 
 constexpr int64_t kStaticMaxVertices = GR_STATIC_MAX_VERTICES;
 constexpr int64_t kStaticMaxEdges = GR_STATIC_MAX_EDGES;
-constexpr int kStaticBig = GR_DEFAULT_BIG_DEGREE;
+constexpr int kStaticBig = GR_DEFAULT_BIG_DEGREE;  // no medium class here: 32-row batches
 // chunks of one frontier: at most m / chunk + m / kStaticBig + 1 entries
 constexpr int64_t kStaticChunkCap =
     kStaticMaxEdges / GR_CHUNK_EDGES + kStaticMaxEdges / kStaticBig + 2;

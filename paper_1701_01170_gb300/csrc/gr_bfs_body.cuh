@@ -265,7 +265,7 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
       // then short rows 32 at a time (first batch by warp index, further
       // batches from a counter that idle warps never touch)
       auto no_payload = [](int32_t) -> uint32_t { return 0u; };
-      gr_chunks_loop<GR_VISIT_STRIPS>(ch, nch, &ctl->workc[s0], swarp, (int)nwarps, lane, a.R, a.C,
+      gr_chunks_loop<GR_VISIT_STRIPS>(ch, nch, swarp, (int)nwarps, lane, a.R, a.C,
                                       cnt, no_payload, pre, visit);
       if (a.qm[0])
         gr_rows_loop<GR_VISIT_STRIPS>(a.qm[L & 1], nqm, GR_MEDIUM_BATCH, &ctl->workm[s0], swarp,

@@ -35,7 +35,13 @@
 #endif
 
 // Library defaults (tunable per call through gr_bfs_opts / gr_sssp_opts).
-#define GR_DEFAULT_BIG_DEGREE 1024   // rows >= this are split into edge chunks
+// Rows of at least the split threshold are expanded as edge chunks.  A warp
+// batch of medium rows then holds at most GR_MEDIUM_BATCH * threshold edges,
+// which should stay near 16 rounds of the body's strips: BFS relaxes 2
+// strips (64 edges) per round, SSSP bulk steps 8 (256 edges).
+#define GR_DEFAULT_BFS_BIG 256
+#define GR_DEFAULT_SSSP_BIG 1024
+#define GR_DEFAULT_BIG_DEGREE GR_DEFAULT_SSSP_BIG
 #ifndef GR_CHUNK_EDGES
 #define GR_CHUNK_EDGES 256           // edges per chunk of a split row
 #endif
@@ -532,19 +538,37 @@ __device__ __forceinline__ void gr_rows_loop(const int32_t* list, int len, int p
   }
 }
 
-// Static-first / dynamic loop over the edge chunks of split rows.
+// Loop over the edge chunks of split rows.  Chunks hold at most
+// GR_CHUNK_EDGES edges each, so they are dealt out statically (warp w takes
+// chunks w, w + nwarps, ...; no counter), and each warp prefetches two chunks
+// ahead: the entry of chunk c + 2 * nwarps and the row end and payload of
+// chunk c + nwarps are in flight while chunk c is expanded.
 template <int U, class Payload, class Pre, class Edge>
-__device__ __forceinline__ void gr_chunks_loop(const int2* ch, int nch, int* counter, int swarp,
-                                               int nwarps, int lane,
-                                               const int32_t* __restrict__ R,
+__device__ __forceinline__ void gr_chunks_loop(const int2* ch, int nch, int swarp, int nwarps,
+                                               int lane, const int32_t* __restrict__ R,
                                                const int32_t* __restrict__ C, GrCounters& cnt,
                                                Payload&& payload, Pre&& pre, Edge&& edge) {
-  for (int c = swarp; c < nch; c = gr_next_batch(c, nch, nwarps, counter, 1, lane)) {
-    const int2 cu = __ldcg(ch + c);
-    const int e1 = min(cu.y + GR_CHUNK_EDGES, __ldg(R + cu.x + 1));
-    const uint32_t pl = payload(cu.x);
+  int c = swarp;
+  if (c >= nch) return;
+  int2 cur = __ldcg(ch + c);
+  int2 nxt = c + nwarps < nch ? __ldcg(ch + c + nwarps) : make_int2(0, 0);
+  int cur_end = min(cur.y + GR_CHUNK_EDGES, __ldg(R + cur.x + 1));
+  uint32_t cur_pl = payload(cur.x);
+  for (; c < nch; c += nwarps) {
+    const int cn = c + nwarps, cnn = c + 2 * nwarps;
+    const int2 nn = cnn < nch ? __ldcg(ch + cnn) : make_int2(0, 0);
+    int nxt_end = 0;
+    uint32_t nxt_pl = 0;
+    if (cn < nch) {
+      nxt_end = min(nxt.y + GR_CHUNK_EDGES, __ldg(R + nxt.x + 1));
+      nxt_pl = payload(nxt.x);
+    }
     if (lane == 0) ++cnt.verts;
-    gr_warp_chunk_u<U>(C, cu.x, cu.y, e1, pl, lane, pre, edge);
+    gr_warp_chunk_u<U>(C, cur.x, cur.y, cur_end, cur_pl, lane, pre, edge);
+    cur = nxt;
+    cur_end = nxt_end;
+    cur_pl = nxt_pl;
+    nxt = nn;
   }
 }
 

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(NT, GR_SSSP_MIN_BLOCKS) sssp_persistent(SsspAr
 extern "C" void gr_sssp_opts_default(gr_sssp_opts* o) {
   if (!o) return;
   o->delta = 0;
-  o->big_degree = GR_DEFAULT_BIG_DEGREE;
+  o->big_degree = GR_DEFAULT_SSSP_BIG;
   o->blocks_per_sm = 0;
   o->spin_limit = GR_DEFAULT_SPIN_LIMIT;
   o->ws = nullptr;
@@ -92,7 +92,7 @@ extern "C" gr_status gr_sssp(const gr_graph* g, int32_t src, uint32_t* dist, int
   a.status = ws->status;
   a.src = src;
   a.delta = o.delta ? o.delta : default_delta(g);
-  a.big = o.big_degree > 0 ? (o.big_degree < 32 ? 32 : o.big_degree) : GR_DEFAULT_BIG_DEGREE;
+  a.big = o.big_degree > 0 ? (o.big_degree < 32 ? 32 : o.big_degree) : GR_DEFAULT_SSSP_BIG;
   a.track_deg = g->max_degree >= GR_MEDIUM_DEGREE;
   a.spin = o.spin_limit ? o.spin_limit : GR_DEFAULT_SPIN_LIMIT;
   a.level_stats = o.level_stats;

@@ -30,7 +30,7 @@ from . import (GR_OP_BFS, GR_OP_SSSP, batch_opts, bfs_opts, gr_batch_create, gr_
 BFS_GRID = {
     "do_a": [0.002, 0.01, 0.05, 0.2],
     "do_b": [0.0, 0.05],
-    "big_degree": [256, 1024, 4096],
+    "big_degree": [64, 256, 1024],
     "blocks_per_sm": [0, 2],
 }
 SSSP_DELTA_FACTORS = [0.25, 0.5, 1.0, 2.0, 4.0, 8.0]
@@ -41,7 +41,7 @@ BATCH_CLUSTERS = [1, 2, 4, 8]
 class BfsChoice:
     do_a: float = 0.05
     do_b: float = 0.05
-    big_degree: int = 1024
+    big_degree: int = 256
     blocks_per_sm: int = 0
     ms: float = float("nan")
 
