@@ -43,7 +43,8 @@ L2_FLUSH_BYTES = 512 << 20   # larger than the 126 MB L2
 def parse_args():
     p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=1 + N_RANDOM_SOURCES,
+                   help="timed steps; the default runs every source (hub + 64 random) once")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--scale", type=int, default=SCALE, help="R-MAT scale (22 = the named workload)")
@@ -171,12 +172,16 @@ def oracle_queries(g, srcs, threads):
 
 
 def cpu_baseline(g, srcs):
+    """Throughput of the oracle on all host cores, plus its one-thread latency."""
     threads = host_threads(g)
     sample = [srcs[i % len(srcs)] for i in range(threads)]
     secs, edges = oracle_queries(g, sample, threads)
+    secs1, _ = oracle_queries(g, [srcs[0]], 1)
     return {"value": edges / secs / 1e9, "unit": "GTEPS", "cores": threads, "kind": "oracle",
+            "latency_ms_one_thread": secs1 * 1e3,
             "sample": f"{threads} BFS+SSSP query pairs (oracle queue BFS + binary-heap "
-                      f"Dijkstra) on the same graph, one per host thread, {secs:.1f} s wall"}
+                      f"Dijkstra) on the same graph, one per host thread, {secs:.1f} s wall; "
+                      f"latency: one pair from the highest-degree vertex on one thread"}
 
 
 # -------------------------------------------------------------- helpers ---
@@ -423,6 +428,8 @@ def run_ours(args):
                       "sssp_gteps": e_sssp / (sum(t_sssp) / 1e3) / 1e9,
                       "bfs_ms_median": statistics.median(t_bfs),
                       "sssp_ms_median": statistics.median(t_sssp),
+                      "bfs_ms_p99": float(np.percentile(t_bfs, 99)),
+                      "sssp_ms_p99": float(np.percentile(t_sssp, 99)),
                       "wall_s_timed_loop": wall},
         "roofline": roof[dominant],
         "roofline_other": roof["bfs" if dominant == "sssp" else "sssp"],

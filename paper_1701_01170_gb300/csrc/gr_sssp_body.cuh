@@ -15,6 +15,9 @@
 #define GR_BULK_STRIPS 8   // 32-edge strips a warp relaxes per round in bulk steps
 #endif
 
+#ifndef GR_COLLECT_WORDS
+#define GR_COLLECT_WORDS 4  // non-empty bitmap words a warp collects per round
+#endif
 // Bulk steps (fire-and-forget atomics and a label-change bitmap, then one
 // pass over the bitmap builds the next piles) pay one extra barrier and a
 // pass over n bits, so by default they start at n / GR_BULK_DIVISOR near rows
@@ -157,18 +160,22 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
     const int next_stamp = it + 1;
 
     // append to the next near frontier — all lanes call this
-    auto near_append = [&](bool take, int32_t v) {
-      int vbeg = 0, vdeg = 0;
-      if (take && a.track_deg) {
-        vbeg = __ldg(a.R + v);
-        vdeg = __ldg(a.R + v + 1) - vbeg;
-      }
+    // (vbeg, vdeg: the row of v when the caller has loaded it already)
+    auto near_append_row = [&](bool take, int32_t v, int vbeg, int vdeg) {
       const bool big = take && vdeg >= a.big;
       const bool mid = take && !big && qmn && vdeg >= GR_MEDIUM_DEGREE;
       near_stage.append(qn, &ctl->qlen[s1], a.n, take && !big && !mid, v, lane);
       mid_stage.append(qmn, &ctl->qmlen[s1], a.n, mid, v, lane);
       if (big)
         bstage.add(chn, a.chunk_cap, &ctl->nchunk[s1], &ctl->nbig[s1], v, vbeg, vdeg, a.status);
+    };
+    auto near_append = [&](bool take, int32_t v) {
+      int vbeg = 0, vdeg = 0;
+      if (take && a.track_deg) {
+        vbeg = __ldg(a.R + v);
+        vdeg = __ldg(a.R + v + 1) - vbeg;
+      }
+      near_append_row(take, v, vbeg, vdeg);
     };
     // join the next near frontier (once per step) — all lanes call this
     auto to_near = [&](bool take, int32_t v) {
@@ -245,26 +252,51 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
         uint32_t word = w < nwords ? __ldcg(a.touched + w) : 0u;
         if (word) a.touched[w] = 0u;
         unsigned nz = __ballot_sync(GR_FULL_MASK, word != 0u);
+        // four non-empty words per round: their labels, then the rows of the
+        // near ones, are loaded together
+        constexpr int KW = GR_COLLECT_WORDS;
         while (nz) {
-          const int j = __ffs(nz) - 1;
-          nz &= nz - 1u;
-          const uint32_t bits = __shfl_sync(GR_FULL_MASK, word, j);
-          const bool mine = (bits >> lane) & 1u;
-          const int32_t v = (wb + j) * 32 + lane;
-          unsigned d = 0;
-          if (mine) {
-            ++cnt.updates;
-            d = (unsigned)(__ldcg(a.key + v) >> 32);
+          bool mine[KW];
+          int32_t v[KW];
+          unsigned d[KW];
+#pragma unroll
+          for (int k = 0; k < KW; ++k) {
+            const int j = nz ? __ffs(nz) - 1 : -1;
+            if (nz) nz &= nz - 1u;
+            const uint32_t bits = __shfl_sync(GR_FULL_MASK, word, j < 0 ? 0 : j);
+            mine[k] = j >= 0 && ((bits >> lane) & 1u);
+            v[k] = (wb + (j < 0 ? 0 : j)) * 32 + lane;
           }
-          near_append(mine && d < T, v);
-          bool far = mine && d >= T;
-          if (far) {
-            far = a.stamp_far[v] != fe;  // this thread owns v in this pass
-            if (far) a.stamp_far[v] = fe;
+#pragma unroll
+          for (int k = 0; k < KW; ++k) {
+            d[k] = 0;
+            if (mine[k]) {
+              ++cnt.updates;
+              d[k] = (unsigned)(__ldcg(a.key + v[k]) >> 32);
+            }
           }
-          far_stage.append(a.far[fe & 1], &ctl->farlen[fe % 3], a.n, far, v, lane);
-          const unsigned mn = gr_warp_min_u32(far ? d : UINT_MAX);
-          if (lane == 0 && mn != UINT_MAX) atomicMin(&s_farmin, mn);
+          int vb[KW], vd[KW];
+#pragma unroll
+          for (int k = 0; k < KW; ++k) {
+            vb[k] = 0;
+            vd[k] = 0;
+            if (mine[k] && d[k] < T && a.track_deg) {
+              vb[k] = __ldg(a.R + v[k]);
+              vd[k] = __ldg(a.R + v[k] + 1) - vb[k];
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < KW; ++k) {
+            near_append_row(mine[k] && d[k] < T, v[k], vb[k], vd[k]);
+            bool far = mine[k] && d[k] >= T;
+            if (far) {
+              far = a.stamp_far[v[k]] != fe;  // this thread owns v in this pass
+              if (far) a.stamp_far[v[k]] = fe;
+            }
+            far_stage.append(a.far[fe & 1], &ctl->farlen[fe % 3], a.n, far, v[k], lane);
+            const unsigned mn = gr_warp_min_u32(far ? d[k] : UINT_MAX);
+            if (lane == 0 && mn != UINT_MAX) atomicMin(&s_farmin, mn);
+          }
         }
       }
     } else if (nrows > 0) {
