@@ -93,10 +93,10 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
   __shared__ int s_nq, s_nqm, s_nch, s_nbig;
   __shared__ unsigned long long s_mf;
   __shared__ int s_qcnt, s_qbase, s_ucnt, s_ubase, s_nu;
-  GrStage stage{ar.buf0, &s_qcnt, &s_qbase};
+  GrStage stage{ar.buf0, &s_qcnt, &s_qbase, GR_STAGE_CAP};
   __shared__ int s_mcnt, s_mbase;
-  GrStage mstage{ar.bufm, &s_mcnt, &s_mbase};
-  GrStage ustage{ar.buf1, &s_ucnt, &s_ubase};
+  GrStage mstage{ar.bufm, &s_mcnt, &s_mbase, GR_STAGE_CAP};
+  GrStage ustage{ar.buf1, &s_ucnt, &s_ubase, GR_STAGE_CAP};
   __shared__ int s_bcnt, s_btot[2];
   GrBigStage bstage{ar.bv, ar.bb, ar.bd, ar.bo, &s_bcnt, s_btot};
   __shared__ unsigned long long s_mfsum;

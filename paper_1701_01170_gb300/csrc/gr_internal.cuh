@@ -259,7 +259,9 @@ __device__ __forceinline__ int gr_next_batch(int cur, int total, int static_span
   return static_span + gr_warp_grab(counter, amount, lane);
 }
 
-#define GR_PULL_WORDS 4
+#ifndef GR_PULL_WORDS
+#define GR_PULL_WORDS 4  // bitmap words (32 candidates each) per pull batch and warp
+#endif
 // Rows are expanded in three classes (the paper's TWC classes, Sec. 5.1.2):
 // rows shorter than GR_MEDIUM_DEGREE in batches of 32 per warp, medium rows
 // in batches of GR_MEDIUM_BATCH per warp, rows of at least the split
@@ -379,9 +381,10 @@ __device__ __forceinline__ void gr_warp_set_bit(uint32_t* bm, bool set, int32_t 
 // to global memory.
 #define GR_STAGE_CAP 2048
 struct GrStage {
-  int* buf;  // shared, GR_STAGE_CAP entries
+  int* buf;  // shared, cap entries
   int* cnt;  // shared
   int* base; // shared
+  int cap;
   // one thread; a __syncthreads must follow before the first append
   __device__ __forceinline__ void reset() { *cnt = 0; }
   // all 32 lanes
@@ -394,20 +397,32 @@ struct GrStage {
     if (lane == leader) b = atomicAdd(cnt, __popc(mask));
     b = __shfl_sync(GR_FULL_MASK, b, leader);
     const int pos = b + __popc(mask & ((1u << lane) - 1u));
-    const bool over = take && pos >= GR_STAGE_CAP;
+    const bool over = take && pos >= cap;
     if (take && !over) buf[pos] = v;
     gr_warp_append(gq, glen, gcap, over, v, lane);
   }
   // every thread of the CTA
   __device__ __forceinline__ void flush(int32_t* gq, int* glen, int64_t gcap) {
     __syncthreads();
-    const int c = min(*cnt, GR_STAGE_CAP);
+    const int c = min(*cnt, cap);
     if (threadIdx.x == 0) *base = c > 0 ? atomicAdd(glen, c) : 0;
     __syncthreads();
     const int b = *base;
     for (int i = threadIdx.x; i < c; i += blockDim.x)
       if (b + i < gcap) gq[b + i] = buf[i];
   }
+};
+
+// Larger staging buffers for a kernel that runs one CTA per SM (SSSP): its
+// steps append up to a few thousand vertices per CTA, more than the static
+// arena holds.  Lives in dynamic shared memory.
+#define GR_BIG_NEAR_CAP 16384
+#define GR_BIG_MID_CAP 8192
+#define GR_BIG_FAR_CAP 8192
+struct GrStageBufs {
+  int near[GR_BIG_NEAR_CAP];
+  int mid[GR_BIG_MID_CAP];
+  int far[GR_BIG_FAR_CAP];
 };
 
 // Warp-centric expansion of the rows of up to 32 sources (one per lane):

@@ -30,11 +30,15 @@ constexpr int NT = GR_PERSIST_THREADS;
 #ifndef GR_SSSP_MIN_BLOCKS
 #define GR_SSSP_MIN_BLOCKS 1
 #endif
+#ifndef GR_SSSP_BIG_STAGE
+#define GR_SSSP_BIG_STAGE 1  // staging buffers in dynamic shared memory (else the static arena)
+#endif
 __global__ void __launch_bounds__(NT, GR_SSSP_MIN_BLOCKS) sssp_persistent(SsspArgs a) {
   GridScope sc{a.ctl, a.status, a.spin, (int64_t)blockIdx.x * NT + threadIdx.x,
                (int64_t)gridDim.x * NT, 0u};
   __shared__ GrArena ar;
-  gr_sssp_body(a, sc, ar);
+  extern __shared__ GrStageBufs big[];  // one CTA per SM: room for large staging buffers
+  gr_sssp_body(a, sc, ar, GR_SSSP_BIG_STAGE ? big : nullptr);
 }
 
 }  // namespace
@@ -98,12 +102,18 @@ extern "C" gr_status gr_sssp(const gr_graph* g, int32_t src, uint32_t* dist, int
   a.level_stats = o.level_stats;
   a.max_levels = o.max_levels;
 
-  const int blocks = gr_launch_blocks((const void*)sssp_persistent, NT, 0, g->num_sms,
+  const size_t smem = sizeof(GrStageBufs);
+  if (cudaFuncSetAttribute((const void*)sssp_persistent,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return GR_ERR_CUDA;
+  }
+  const int blocks = gr_launch_blocks((const void*)sssp_persistent, NT, smem, g->num_sms,
                                       o.blocks_per_sm);
   if (blocks <= 0) return GR_ERR_CUDA;
   if (gr_reset_ctl(ws, s) != cudaSuccess) return GR_ERR_CUDA;
   void* args[] = {&a};
-  if (cudaLaunchCooperativeKernel((const void*)sssp_persistent, dim3(blocks), dim3(NT), args, 0,
+  if (cudaLaunchCooperativeKernel((const void*)sssp_persistent, dim3(blocks), dim3(NT), args, smem,
                                   s) != cudaSuccess) {
     (void)cudaGetLastError();
     return GR_ERR_CUDA;

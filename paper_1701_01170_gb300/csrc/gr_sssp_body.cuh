@@ -60,7 +60,8 @@ struct SsspArgs {
 constexpr unsigned long long GR_KEY_INF = ~0ull;
 
 template <class S>
-__device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& ar) {
+__device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& ar,
+                                             GrStageBufs* big = nullptr) {
   const int lane = threadIdx.x & 31;
   const int64_t gtid = sc.tid;
   const int64_t gthreads = sc.nthreads;
@@ -105,10 +106,13 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
   __shared__ unsigned s_fm;
   __shared__ int s_ncnt, s_nbase, s_fcnt, s_fbase;
   __shared__ unsigned s_farmin;
-  GrStage near_stage{ar.buf0, &s_ncnt, &s_nbase};
+  GrStage near_stage{big ? big->near : ar.buf0, &s_ncnt, &s_nbase,
+                     big ? GR_BIG_NEAR_CAP : GR_STAGE_CAP};
   __shared__ int s_mcnt, s_mbase;
-  GrStage mid_stage{ar.bufm, &s_mcnt, &s_mbase};
-  GrStage far_stage{ar.buf1, &s_fcnt, &s_fbase};
+  GrStage mid_stage{big ? big->mid : ar.bufm, &s_mcnt, &s_mbase,
+                    big ? GR_BIG_MID_CAP : GR_STAGE_CAP};
+  GrStage far_stage{big ? big->far : ar.buf1, &s_fcnt, &s_fbase,
+                    big ? GR_BIG_FAR_CAP : GR_STAGE_CAP};
   __shared__ int s_bcnt, s_btot[2];
   GrBigStage bstage{ar.bv, ar.bb, ar.bd, ar.bo, &s_bcnt, s_btot};
   for (;; ++it) {
