@@ -6,6 +6,7 @@
 // status word; it never traps.
 #include <climits>
 #include <cstdlib>
+#include <mutex>
 #include <cstring>
 #include <new>
 
@@ -264,13 +265,48 @@ cudaError_t gr_reset_ctl(gr_workspace* ws, cudaStream_t s) {
   return cudaMemsetAsync(ws->ctl, 0, sizeof(GrCtl), s);
 }
 
+// Resident CTAs per SM of a persistent kernel.  The occupancy query costs
+// microseconds of host time, which a caller timing a whole query pays in
+// GPU idle time, so results are cached per (device, kernel, threads, shared
+// memory) and the dynamic shared-memory attribute is set once per entry.
+namespace {
+struct OccEntry {
+  int device;
+  const void* kernel;
+  int threads;
+  size_t smem;
+  int per_sm;
+};
+std::mutex g_occ_mutex;
+OccEntry g_occ[64];
+int g_occ_n = 0;
+}  // namespace
+
 int gr_launch_blocks(const void* kernel, int threads, size_t smem, int num_sms, int requested) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
-          cudaSuccess ||
-      per_sm < 1) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
     (void)cudaGetLastError();
     return 0;
+  }
+  int per_sm = 0;
+  {
+    std::lock_guard<std::mutex> lock(g_occ_mutex);
+    for (int i = 0; i < g_occ_n; ++i)
+      if (g_occ[i].device == dev && g_occ[i].kernel == kernel && g_occ[i].threads == threads &&
+          g_occ[i].smem == smem)
+        per_sm = g_occ[i].per_sm;
+    if (per_sm == 0) {
+      if ((smem > 48 * 1024 &&
+           cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+               cudaSuccess) ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
+              cudaSuccess ||
+          per_sm < 1) {
+        (void)cudaGetLastError();
+        return 0;
+      }
+      if (g_occ_n < 64) g_occ[g_occ_n++] = OccEntry{dev, kernel, threads, smem, per_sm};
+    }
   }
   if (requested > 0 && requested < per_sm) per_sm = requested;
   return per_sm * num_sms;

@@ -30,7 +30,7 @@ namespace {
 constexpr int NT = GR_PERSIST_THREADS;
 
 #ifndef GR_BFS_MIN_BLOCKS
-#define GR_BFS_MIN_BLOCKS 3  // resident CTAs per SM the register budget is sized for
+#define GR_BFS_MIN_BLOCKS 2  // resident CTAs per SM the register budget is sized for
 #endif
 __global__ void __launch_bounds__(NT, GR_BFS_MIN_BLOCKS) bfs_persistent(BfsArgs a) {
   GridScope sc{a.ctl, a.status, a.spin, (int64_t)blockIdx.x * NT + threadIdx.x,

@@ -9,7 +9,7 @@
 #include "gr_internal.cuh"
 
 #ifndef GR_VISIT_STRIPS
-#define GR_VISIT_STRIPS 2  // 32-edge strips a warp expands per round
+#define GR_VISIT_STRIPS 4  // 32-edge strips a warp expands per round
 #endif
 
 struct BfsArgs {

@@ -37,8 +37,8 @@
 // Library defaults (tunable per call through gr_bfs_opts / gr_sssp_opts).
 // Rows of at least the split threshold are expanded as edge chunks.  A warp
 // batch of medium rows then holds at most GR_MEDIUM_BATCH * threshold edges,
-// which should stay near 16 rounds of the body's strips: BFS relaxes 2
-// strips (64 edges) per round, SSSP bulk steps 8 (256 edges).
+// which should stay within about 16 rounds of the body's strips: BFS
+// expands 4 strips (128 edges) per round, SSSP bulk steps 8 (256 edges).
 #define GR_DEFAULT_BFS_BIG 256
 #define GR_DEFAULT_SSSP_BIG 1024
 #define GR_DEFAULT_BIG_DEGREE GR_DEFAULT_SSSP_BIG

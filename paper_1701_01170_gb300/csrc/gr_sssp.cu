@@ -102,12 +102,7 @@ extern "C" gr_status gr_sssp(const gr_graph* g, int32_t src, uint32_t* dist, int
   a.level_stats = o.level_stats;
   a.max_levels = o.max_levels;
 
-  const size_t smem = sizeof(GrStageBufs);
-  if (cudaFuncSetAttribute((const void*)sssp_persistent,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-    (void)cudaGetLastError();
-    return GR_ERR_CUDA;
-  }
+  const size_t smem = sizeof(GrStageBufs);  // the dynamic shared-memory limit is raised once
   const int blocks = gr_launch_blocks((const void*)sssp_persistent, NT, smem, g->num_sms,
                                       o.blocks_per_sm);
   if (blocks <= 0) return GR_ERR_CUDA;
