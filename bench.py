@@ -55,8 +55,9 @@ def parse_args():
     p.add_argument("--workload", choices=["s22", "s16", "grid", "msbfs", "batch", "serve"],
                    default="s22",
                    help="s22 (default, the headline workload) or one of the other configurations")
-    p.add_argument("--rates", default="2000,5000,10000,20000,50000",
-                   help="serve: Poisson arrival rates (requests/s)")
+    p.add_argument("--rates", default="20,2000,5000,10000,20000,50000",
+                   help="serve: Poisson arrival rates (requests/s); the first one is below "
+                        "the service rate (unloaded latency), the others saturate it")
     p.add_argument("--requests", type=int, default=400, help="serve: requests per rate")
     return p.parse_args()
 
@@ -657,10 +658,12 @@ def run_serve(args, gr, base):
     graphs = {name: gr.Graph.from_csr(g) for name, g in wl.serving_graphs()}
     cands = {name: np.flatnonzero(np.diff(G.R.cpu().numpy()) > 0) for name, G in graphs.items()}
     multi = [n for n in graphs if n.startswith("rmat")]
-    lanes = 4
+    lanes = 8
     be = serve.GpuBackend(graphs, lanes, blocks_per_sm=1)
     be.prepare_multi(multi)
-    budget = 16 << 30
+    caps = be.calibrate([n for n in graphs if n not in multi],
+                        {n: int(cands[n][0]) for n in graphs})
+    budget = 96 << 30     # per-lane workspaces; the graphs themselves take about 9 GB
     names = sorted(graphs)
     results = []
     for rate in [float(x) for x in args.rates.split(",")]:
@@ -681,7 +684,7 @@ def run_serve(args, gr, base):
           "config": {"workload": "serving: 8 resident graphs (R-MAT s18/20/22/24 ef16, grids "
                                  "1024^2..8192^2), Poisson BFS/SSSP 50/50, random sources, "
                                  f"{args.requests} requests per rate, {lanes} lanes, "
-                                 "16 GB budget"},
+                                 "96 GB workspace budget", "cta_caps": caps},
           "per_rate": results})
 
 

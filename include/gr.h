@@ -269,6 +269,11 @@ typedef struct gr_bfs_opts {
                             (frontier size, 1 if pull, sum of the frontier's
                             degrees m_f, start time in ns after level 0)   */
   int32_t max_levels;    /* capacity of level_stats in levels                 */
+  int32_t max_blocks;    /* upper bound on the persistent grid's CTAs; 0 = none.
+                            A query on a high-diameter graph (small frontiers,
+                            latency-bound levels) loses little on a quarter
+                            of the SMs, and several such queries on separate
+                            streams then run side by side                   */
 } gr_bfs_opts;
 
 /* Fill *o with the library defaults. */
@@ -302,6 +307,7 @@ typedef struct gr_sssp_opts {
                             builds the next piles; smaller ones enqueue per
                             edge.  0 = default (n / 64, at least 4096),
                             < 0 = never                                      */
+  int32_t max_blocks;    /* as in gr_bfs_opts                                  */
 } gr_sssp_opts;
 
 void gr_sssp_opts_default(gr_sssp_opts* o);

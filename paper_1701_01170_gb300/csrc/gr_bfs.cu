@@ -52,6 +52,7 @@ extern "C" void gr_bfs_opts_default(gr_bfs_opts* o) {
   o->ws = nullptr;
   o->level_stats = nullptr;
   o->max_levels = 0;
+  o->max_blocks = 0;
 }
 
 extern "C" gr_status gr_bfs(const gr_graph* g, int32_t src, int32_t* depth, int32_t* pred,
@@ -61,7 +62,7 @@ extern "C" gr_status gr_bfs(const gr_graph* g, int32_t src, int32_t* depth, int3
   gr_bfs_opts_default(&o);
   if (opts) o = *opts;
   if (o.direction < GR_DIR_AUTO || o.direction > GR_DIR_PULL || o.max_levels < 0 ||
-      (o.max_levels > 0 && !o.level_stats))
+      (o.max_levels > 0 && !o.level_stats) || o.max_blocks < 0)
     return GR_ERR_INVALID_ARG;
   const bool symmetric = (g->flags & GR_SYMMETRIC) != 0;
   if (o.direction == GR_DIR_PULL && !symmetric) return GR_ERR_UNSUPPORTED;
@@ -101,9 +102,10 @@ extern "C" gr_status gr_bfs(const gr_graph* g, int32_t src, int32_t* depth, int3
   a.level_stats = o.level_stats;
   a.max_levels = o.max_levels;
 
-  const int blocks = gr_launch_blocks((const void*)bfs_persistent, NT, 0, g->num_sms,
-                                      o.blocks_per_sm);
+  int blocks = gr_launch_blocks((const void*)bfs_persistent, NT, 0, g->num_sms,
+                                o.blocks_per_sm);
   if (blocks <= 0) return GR_ERR_CUDA;
+  if (o.max_blocks > 0 && blocks > o.max_blocks) blocks = o.max_blocks;
   if (gr_reset_ctl(ws, s) != cudaSuccess) return GR_ERR_CUDA;
   void* args[] = {&a};
   if (cudaLaunchCooperativeKernel((const void*)bfs_persistent, dim3(blocks), dim3(NT), args, 0,

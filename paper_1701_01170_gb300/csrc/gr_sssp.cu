@@ -53,6 +53,7 @@ extern "C" void gr_sssp_opts_default(gr_sssp_opts* o) {
   o->level_stats = nullptr;
   o->max_levels = 0;
   o->bulk_rows = 0;
+  o->max_blocks = 0;
 }
 
 // Bucket width from the graph: about one warp's worth of average edges
@@ -66,7 +67,8 @@ extern "C" gr_status gr_sssp(const gr_graph* g, int32_t src, uint32_t* dist, int
   gr_sssp_opts o;
   gr_sssp_opts_default(&o);
   if (opts) o = *opts;
-  if (o.max_levels < 0 || (o.max_levels > 0 && !o.level_stats)) return GR_ERR_INVALID_ARG;
+  if (o.max_levels < 0 || (o.max_levels > 0 && !o.level_stats) || o.max_blocks < 0)
+    return GR_ERR_INVALID_ARG;
   gr_workspace* ws = gr_resolve_ws(g, o.ws);
   if (!ws || ws->g != g || !ws->key) return GR_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -103,9 +105,10 @@ extern "C" gr_status gr_sssp(const gr_graph* g, int32_t src, uint32_t* dist, int
   a.max_levels = o.max_levels;
 
   const size_t smem = sizeof(GrStageBufs);  // the dynamic shared-memory limit is raised once
-  const int blocks = gr_launch_blocks((const void*)sssp_persistent, NT, smem, g->num_sms,
-                                      o.blocks_per_sm);
+  int blocks = gr_launch_blocks((const void*)sssp_persistent, NT, smem, g->num_sms,
+                                o.blocks_per_sm);
   if (blocks <= 0) return GR_ERR_CUDA;
+  if (o.max_blocks > 0 && blocks > o.max_blocks) blocks = o.max_blocks;
   if (gr_reset_ctl(ws, s) != cudaSuccess) return GR_ERR_CUDA;
   void* args[] = {&a};
   if (cudaLaunchCooperativeKernel((const void*)sssp_persistent, dim3(blocks), dim3(NT), args, smem,

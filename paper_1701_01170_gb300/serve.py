@@ -175,6 +175,34 @@ class GpuBackend:
         self.footprint = {name: (gr_graph_footprint(G.handle, GR_OP_BFS),
                                  gr_graph_footprint(G.handle, GR_OP_SSSP))
                           for name, G in graphs.items()}
+        self.graph_blocks: dict[str, int] = {}   # name -> CTA cap of its queries (0: none)
+
+    def calibrate(self, names, srcs: dict, slack: float = 1.5):
+        """Cap the CTAs of a graph's queries at SMs / lanes when that costs a query at
+        most `slack` times its full-GPU time (latency-bound, high-diameter graphs), so
+        that the lanes run such queries side by side instead of one at a time."""
+        from . import gr_bfs
+        torch = self.torch
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        cap = max(1, sms // len(self.streams))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+        def once(G, src, opts):
+            out = self.dev_out[0][:G.n]
+            gr_bfs(G.handle, src, out, None, opts)       # warm
+            ev[0].record()
+            gr_bfs(G.handle, src, out, None, opts)
+            ev[1].record()
+            ev[1].synchronize()
+            return ev[0].elapsed_time(ev[1])
+
+        for name in names:
+            G = self.graphs[name]
+            full = once(G, srcs[name], self._bo(blocks_per_sm=self.blocks_per_sm))
+            capped = once(G, srcs[name], self._bo(blocks_per_sm=self.blocks_per_sm,
+                                                  max_blocks=cap))
+            self.graph_blocks[name] = cap if capped <= slack * full else 0
+        return dict(self.graph_blocks)
 
     def graph_infos(self, multi_names) -> dict[str, GraphInfo]:
         out = {}
@@ -239,12 +267,15 @@ class GpuBackend:
             ws = self._workspace(lane, unit.graph, unit.op)
             r = unit.requests[0]
             out = self.dev_out[lane][:G.n]
+            cap = self.graph_blocks.get(unit.graph, 0)
             if unit.op == OP_BFS:
                 gr_bfs(G.handle, r.src, out, None,
-                       self._bo(ws=ws, blocks_per_sm=self.blocks_per_sm, **self.bfs_opts), s)
+                       self._bo(ws=ws, blocks_per_sm=self.blocks_per_sm, max_blocks=cap,
+                                **self.bfs_opts), s)
             else:
                 gr_sssp(G.handle, r.src, out, None,
-                        self._so(ws=ws, blocks_per_sm=self.blocks_per_sm, **self.sssp_opts), s)
+                        self._so(ws=ws, blocks_per_sm=self.blocks_per_sm, max_blocks=cap,
+                                 **self.sssp_opts), s)
             hv = self.host_out[lane][:G.n]
             hv.copy_(out, non_blocking=True)
             s.synchronize()

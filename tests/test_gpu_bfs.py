@@ -208,6 +208,44 @@ def test_barrier_timeout_is_reported_and_recoverable(gr, s16):
     check(g, 0, d, p)
 
 
+@pytest.mark.parametrize("cap", [1, 7, 38])
+def test_cta_cap_does_not_change_depths(gr, s16, cap):
+    g, G = s16
+    for src in (0, 12345):
+        d, p = run_bfs(gr, G, src, max_blocks=cap)
+        check(g, src, d, p)
+    mesh = gg.grid(128, 0.1, seed=4)
+    M = gr.Graph.from_csr(mesh)
+    d, p = run_bfs(gr, M, 0, max_blocks=cap)
+    check(mesh, 0, d, p)
+    M.close()
+
+
+def test_capped_queries_run_side_by_side(gr):
+    # four capped BFS on four streams with their own workspaces at once
+    import torch
+    g = gg.grid(256, 0.1, seed=4)
+    G = gr.Graph.from_csr(g)
+    srcs = [0, 999, 30000, 65535]
+    wss = [gr.gr_workspace_create(G.handle, gr.GR_OP_BFS) for _ in srcs]
+    streams = [torch.cuda.Stream() for _ in srcs]
+    outs = []
+    torch.cuda.synchronize()
+    for src, ws, s in zip(srcs, wss, streams):
+        d = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        p = torch.empty_like(d)
+        gr.gr_bfs(G.handle, src, d, p, gr.bfs_opts(ws=ws, blocks_per_sm=1, max_blocks=16), stream=s)
+        outs.append((d, p))
+    torch.cuda.synchronize()
+    for src, ws, (d, p) in zip(srcs, wss, outs):
+        assert G.sync_status(ws) == 0
+        check(g, src, host(d), host(p))
+        gr.gr_workspace_destroy(ws)
+    with pytest.raises(gr.GrError):
+        gr.gr_bfs(G.handle, 0, outs[0][0], None, gr.bfs_opts(max_blocks=-1))
+    G.close()
+
+
 def test_separate_workspaces_on_streams(gr, s16):
     import torch
     g, G = s16

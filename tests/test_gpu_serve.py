@@ -40,6 +40,9 @@ def test_served_results_equal_solo_results(setup):
     multi = [n for n in names if n.startswith("rmat")]
     be = serve.GpuBackend(graphs, lanes=3, blocks_per_sm=1)
     be.prepare_multi(multi)
+    caps = be.calibrate([n for n in names if n not in multi],
+                        {n: int(cands[n][0]) for n in names}, slack=1e9)
+    assert all(c > 0 for c in caps.values())     # capped queries run side by side below
     infos = be.graph_infos(set(multi))
     # a budget below the sum of all workspaces: admission must evict and wait
     budget = sum(i.bytes_multi for i in infos.values() if i.multi_ok) + \

@@ -86,6 +86,14 @@ def test_bulk_and_per_edge_steps_agree(gr, s16w, bulk, delta):
         check(g, src, d, p)
 
 
+@pytest.mark.parametrize("cap", [1, 7, 38])
+def test_cta_cap_does_not_change_distances(gr, s16w, cap):
+    g, G = s16w
+    for src in (gg.max_degree_vertex(g), 4321):
+        d, p = run_sssp(gr, G, src, max_blocks=cap)
+        check(g, src, d, p)
+
+
 @pytest.mark.parametrize("big", [32, 1 << 30])
 def test_split_thresholds_agree(gr, s16w, big):
     g, G = s16w
