@@ -553,52 +553,6 @@ __device__ __forceinline__ void gr_rows_loop(const int32_t* list, int len, int p
   }
 }
 
-// Two chunks at once (rows ua and ub), U strips each: all 2U column loads,
-// then all 2U per-edge loads, then the functor, so a warp keeps twice as
-// many independent loads in flight as with one chunk.
-template <int U, class Pre, class Edge>
-__device__ __forceinline__ void gr_warp_chunk2_u(const int32_t* __restrict__ C, int32_t ua,
-                                                 int e0a, int e1a, uint32_t pa, int32_t ub,
-                                                 int e0b, int e1b, uint32_t pb, int lane,
-                                                 Pre&& pre, Edge&& edge) {
-  int e[2 * U], v[2 * U];
-  bool act[2 * U];
-#pragma unroll
-  for (int k = 0; k < U; ++k) {
-    e[k] = e0a + k * 32 + lane;
-    act[k] = e[k] < e1a;
-    e[U + k] = e0b + k * 32 + lane;
-    act[U + k] = e[U + k] < e1b;
-  }
-#pragma unroll
-  for (int k = 0; k < 2 * U; ++k) v[k] = act[k] ? GR_LDSTREAM(C + e[k]) : 0;
-  decltype(pre(true, 0, 0)) pv[2 * U];
-#pragma unroll
-  for (int k = 0; k < 2 * U; ++k) pv[k] = pre(act[k], e[k], v[k]);
-#pragma unroll
-  for (int k = 0; k < 2 * U; ++k)
-    edge(act[k], k < U ? ua : ub, k < U ? pa : pb, e[k], v[k], pv[k]);
-}
-
-// Chunk loop taking chunks c and c + nwarps together (gr_warp_chunk2_u).
-template <int U, class Payload, class Pre, class Edge>
-__device__ __forceinline__ void gr_chunks_loop2(const int2* ch, int nch, int swarp, int nwarps,
-                                                int lane, const int32_t* __restrict__ R,
-                                                const int32_t* __restrict__ C, GrCounters& cnt,
-                                                Payload&& payload, Pre&& pre, Edge&& edge) {
-  for (int c = swarp; c < nch; c += 2 * nwarps) {
-    const int c2 = c + nwarps;
-    const int2 a = __ldcg(ch + c);
-    const int2 b = c2 < nch ? __ldcg(ch + c2) : make_int2(a.x, 0);
-    const int ea = min(a.y + GR_CHUNK_EDGES, __ldg(R + a.x + 1));
-    const int eb = c2 < nch ? min(b.y + GR_CHUNK_EDGES, __ldg(R + b.x + 1)) : 0;
-    const uint32_t pa = payload(a.x);
-    const uint32_t pb = c2 < nch ? payload(b.x) : 0u;
-    if (lane == 0) cnt.verts += c2 < nch ? 2 : 1;
-    gr_warp_chunk2_u<U>(C, a.x, a.y, ea, pa, b.x, b.y, eb, pb, lane, pre, edge);
-  }
-}
-
 // Loop over the edge chunks of split rows.  Chunks hold at most
 // GR_CHUNK_EDGES edges each, so they are dealt out statically (warp w takes
 // chunks w, w + nwarps, ...; no counter), and each warp prefetches two chunks

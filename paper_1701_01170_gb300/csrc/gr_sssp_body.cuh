@@ -15,9 +15,6 @@
 #define GR_BULK_STRIPS 8   // 32-edge strips a warp relaxes per round in bulk steps
 #endif
 
-#ifndef GR_BULK_CHUNK_PAIRS
-#define GR_BULK_CHUNK_PAIRS 0  // bulk steps relax two edge chunks per round
-#endif
 #ifndef GR_COLLECT_WORDS
 #define GR_COLLECT_WORDS 4  // non-empty bitmap words a warp collects per round
 #endif
@@ -242,13 +239,8 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
       };
       // largest work first: chunks, medium rows, then short rows
       auto label = [&](int32_t u) -> uint32_t { return (uint32_t)(__ldcg(a.key + u) >> 32); };
-#if GR_BULK_CHUNK_PAIRS
-      gr_chunks_loop2<GR_BULK_STRIPS>(ch, nch, swarp, (int)nwarps, lane, a.R, a.C,
-                                      cnt, label, pre, relax);
-#else
       gr_chunks_loop<GR_BULK_STRIPS>(ch, nch, swarp, (int)nwarps, lane, a.R, a.C,
                                      cnt, label, pre, relax);
-#endif
       if (a.qm[0])
         gr_rows_loop<GR_BULK_STRIPS>(a.qm[it & 1], nqm, GR_MEDIUM_BATCH, &ctl->workm[s0], swarp,
                                      (int)nwarps, lane, a.R, a.C, cnt, label, pre, relax);
