@@ -429,17 +429,26 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
         }
       }
     }
-    stage.flush(qn, &ctl->qlen[s1], a.n);
-    mstage.flush(qmn, &ctl->qmlen[s1], a.n);
-    if (pull && a.ulist[0]) ustage.flush(a.ulist[(L + 1) & 1], &ctl->ulen[s1], a.n);
-    list_ready = pull && a.ulist[0] != nullptr;
-    prev_pull = pull;
-    bstage.flush(chn, a.chunk_cap, &ctl->nchunk[s1], &ctl->nbig[s1], a.status);
+    // combined flush of the level's staged appends: one barrier, then all
+    // global reservations in flight together, then the copies
     my_mf = gr_warp_sum_u64(my_mf);
     if (lane == 0 && my_mf) atomicAdd(&s_mfsum, my_mf);
+    const bool ulist_out = pull && a.ulist[0] != nullptr;
     __syncthreads();
+    bstage.prepare();
+    stage.reserve(&ctl->qlen[s1]);
+    mstage.reserve(&ctl->qmlen[s1]);
+    if (ulist_out) ustage.reserve(&ctl->ulen[s1]);
+    bstage.reserve(&ctl->nchunk[s1], &ctl->nbig[s1]);
     if (threadIdx.x == 0 && s_mfsum) atomicAdd(&ctl->mf[s1], s_mfsum);
     if (threadIdx.x == 0 && s_found) atomicAdd(&ctl->qlen[s1], s_found);
+    __syncthreads();
+    stage.copy_out(qn, a.n);
+    mstage.copy_out(qmn, a.n);
+    if (ulist_out) ustage.copy_out(a.ulist[(L + 1) & 1], a.n);
+    bstage.copy_out(chn, a.chunk_cap, a.status);
+    list_ready = pull && a.ulist[0] != nullptr;
+    prev_pull = pull;
     if (!sc.sync()) return;
   }
   cnt.flush(ctl);

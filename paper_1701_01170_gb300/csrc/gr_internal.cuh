@@ -404,9 +404,21 @@ struct GrStage {
   // every thread of the CTA
   __device__ __forceinline__ void flush(int32_t* gq, int* glen, int64_t gcap) {
     __syncthreads();
-    const int c = min(*cnt, cap);
-    if (threadIdx.x == 0) *base = c > 0 ? atomicAdd(glen, c) : 0;
+    reserve(glen);
     __syncthreads();
+    copy_out(gq, gcap);
+  }
+  // The two halves of flush, for a CTA that flushes several stages at once:
+  // after a __syncthreads, thread 0 reserves every stage's block (the
+  // global atomics are then in flight together); after another
+  // __syncthreads every thread copies.
+  __device__ __forceinline__ void reserve(int* glen) {
+    if (threadIdx.x != 0) return;
+    const int c = min(*cnt, cap);
+    *base = c > 0 ? atomicAdd(glen, c) : 0;
+  }
+  __device__ __forceinline__ void copy_out(int32_t* gq, int64_t gcap) {
+    const int c = min(*cnt, cap);
     const int b = *base;
     for (int i = threadIdx.x; i < c; i += blockDim.x)
       if (b + i < gcap) gq[b + i] = buf[i];
@@ -658,6 +670,15 @@ struct GrBigStage {
   __device__ __forceinline__ void flush(int2* chunks, int64_t cap, int* nchunk, int* nbig,
                                         int* status) {
     __syncthreads();
+    prepare();
+    reserve(nchunk, nbig);
+    __syncthreads();
+    copy_out(chunks, cap, status);
+  }
+  // Split form for a combined flush: prepare() (every thread, after a
+  // __syncthreads; ends with one) lays the CTA's chunks out, reserve() (thread
+  // 0) places them, copy_out() (every thread, after a __syncthreads) writes.
+  __device__ __forceinline__ void prepare() {
     const int c = min(*cnt, GR_BIG_STAGE_CAP);
     if (c == 0) return;  // uniform: every thread read the same count
     if (threadIdx.x == 0) tot[0] = 0;
@@ -665,11 +686,16 @@ struct GrBigStage {
     for (int i = threadIdx.x; i < c; i += blockDim.x)
       off[i] = atomicAdd(&tot[0], (deg[i] + GR_CHUNK_EDGES - 1) / GR_CHUNK_EDGES);
     __syncthreads();
-    if (threadIdx.x == 0) {
-      tot[1] = atomicAdd(nchunk, tot[0]);
-      atomicAdd(nbig, c);
-    }
-    __syncthreads();
+  }
+  __device__ __forceinline__ void reserve(int* nchunk, int* nbig) {
+    const int c = min(*cnt, GR_BIG_STAGE_CAP);
+    if (threadIdx.x != 0 || c == 0) return;
+    tot[1] = atomicAdd(nchunk, tot[0]);
+    atomicAdd(nbig, c);
+  }
+  __device__ __forceinline__ void copy_out(int2* chunks, int64_t cap, int* status) {
+    const int c = min(*cnt, GR_BIG_STAGE_CAP);
+    if (c == 0) return;
     const int gbase = tot[1];
     for (int i = threadIdx.x >> 5; i < c; i += blockDim.x >> 5) {  // a warp per row
       const int nch = (deg[i] + GR_CHUNK_EDGES - 1) / GR_CHUNK_EDGES;

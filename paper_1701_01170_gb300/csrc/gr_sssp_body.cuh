@@ -385,11 +385,20 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
       T = Tn;
       ++fe;
     }
-    near_stage.flush(qn, &ctl->qlen[s1], a.n);
-    mid_stage.flush(qmn, &ctl->qmlen[s1], a.n);
-    bstage.flush(chn, a.chunk_cap, &ctl->nchunk[s1], &ctl->nbig[s1], a.status);
-    far_stage.flush(a.far[fe_out & 1], &ctl->farlen[fe_out % 3], a.n);
+    // combined flush of the step's staged appends: one barrier, then all
+    // global reservations in flight together, then the copies
+    __syncthreads();
+    bstage.prepare();
+    near_stage.reserve(&ctl->qlen[s1]);
+    mid_stage.reserve(&ctl->qmlen[s1]);
+    far_stage.reserve(&ctl->farlen[fe_out % 3]);
+    bstage.reserve(&ctl->nchunk[s1], &ctl->nbig[s1]);
     if (threadIdx.x == 0 && s_farmin != UINT_MAX) atomicMin(&ctl->farmin[fe_out % 3], s_farmin);
+    __syncthreads();
+    near_stage.copy_out(qn, a.n);
+    mid_stage.copy_out(qmn, a.n);
+    far_stage.copy_out(a.far[fe_out & 1], a.n);
+    bstage.copy_out(chn, a.chunk_cap, a.status);
     if (!sc.sync()) return;
   }
   // ---- overflow check: with every unrepresentable candidate dropped, a
