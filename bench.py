@@ -474,10 +474,19 @@ def run_e2e(gr, g, srcs, args, dev, rank):
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
     k = rank_source_offset(rank)
     used = [srcs[(k + i) % len(srcs)] for i in range(steps)]
-    # warm both buffers (first launches, workspaces)
+    # warm both buffers, the copy paths and the pinned result pages (untimed)
     for G, od in zip(Gs, outs_d):
+        with torch.cuda.stream(up):
+            G.R.copy_(hR, non_blocking=True)
+            G.C.copy_(hC, non_blocking=True)
+            G.W.copy_(hW, non_blocking=True)
+        up.synchronize()
         gr.gr_bfs(G.handle, used[0], od[0], od[1])
         gr.gr_sssp(G.handle, used[0], od[2], od[3])
+    with torch.cuda.stream(down):
+        for oh in outs_h:
+            for h, d in zip(oh, outs_d[0]):
+                h.copy_(d, non_blocking=True)
     torch.cuda.synchronize()
     for i, src in enumerate(used):
         b = i & 1

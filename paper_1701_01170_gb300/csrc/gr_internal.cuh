@@ -181,6 +181,33 @@ __device__ __forceinline__ unsigned gr_atom_add_acq_rel(unsigned* p, unsigned v)
   return old;
 }
 
+// Reductions without a return value (PTX red): the issuing warp never
+// waits for them, unlike an atomic whose result register is tracked.
+#ifndef GR_USE_RED
+#define GR_USE_RED 1
+#endif
+__device__ __forceinline__ void gr_red_min_u64(unsigned long long* p, unsigned long long v) {
+#if GR_USE_RED
+  asm volatile("red.relaxed.gpu.global.min.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+#else
+  atomicMin(p, v);
+#endif
+}
+__device__ __forceinline__ void gr_red_or_u64(unsigned long long* p, unsigned long long v) {
+#if GR_USE_RED
+  asm volatile("red.relaxed.gpu.global.or.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+#else
+  atomicOr(p, v);
+#endif
+}
+__device__ __forceinline__ void gr_red_or_u32(uint32_t* p, uint32_t v) {
+#if GR_USE_RED
+  asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+#else
+  atomicOr(p, v);
+#endif
+}
+
 __device__ __forceinline__ int gr_ld_volatile(const int* p) {
   return *(const volatile int*)p;
 }
@@ -364,7 +391,7 @@ __device__ __forceinline__ bool gr_warp_claim(uint32_t* bm, bool active, int32_t
 // atomicOr per distinct word.  All 32 lanes call.
 __device__ __forceinline__ void gr_warp_set_bit(uint32_t* bm, bool set, int32_t v, int lane) {
 #if !GR_CLAIM_AGGREGATE
-  if (set) atomicOr(bm + (v >> 5), 1u << (v & 31));
+  if (set) gr_red_or_u32(bm + (v >> 5), 1u << (v & 31));
   return;
 #endif
   const unsigned wkey = set ? (unsigned)v >> 5 : (0x80000000u | (unsigned)lane);

@@ -146,7 +146,7 @@ __device__ __forceinline__ void push_edge(const MsArgs& a, int32_t u, int32_t v)
 #pragma unroll
   for (int w = 0; w < W; ++w) {
     u64 y = x[w] & ~vis[w];
-    if (y) atomicOr(&a.acc[(size_t)v * W + w], y);
+    if (y) gr_red_or_u64(&a.acc[(size_t)v * W + w], y);
   }
 }
 
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(MS_T) ms_pull_chunks(MsArgs a) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc[w] |= __shfl_xor_sync(GR_FULL_MASK, acc[w], o);
       const u64 y = acc[w] & ~vis[w];
-      if (lane == 0 && y) atomicOr(&a.acc[(size_t)ch.x * W + w], y);
+      if (lane == 0 && y) gr_red_or_u64(&a.acc[(size_t)ch.x * W + w], y);
     }
   }
 }

@@ -230,12 +230,12 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
           } else {
             const unsigned long long cand = (nd << 32) | (unsigned)u;
             if (cand < p.cur) {
-              atomicMin(&a.key[v], cand);
+              gr_red_min_u64(&a.key[v], cand);
               hit = true;
             }
           }
         }
-        if (hit) atomicOr(a.touched + (v >> 5), 1u << (v & 31));
+        if (hit) gr_red_or_u32(a.touched + (v >> 5), 1u << (v & 31));
       };
       // largest work first: chunks, medium rows, then short rows
       auto label = [&](int32_t u) -> uint32_t { return (uint32_t)(__ldcg(a.key + u) >> 32); };
