@@ -637,7 +637,12 @@ def run_other(args):
             jobs.append(gr.gr_job(g=Gs[gi].handle, op=op, src=src, out=o.data_ptr(),
                                   pred=pp.data_ptr()))
         from paper_1701_01170_gb300 import tune
-        best_opts, _ = tune.tune_batch(jobs, reps=2)
+        b0 = gr.gr_batch_create(jobs)                       # library defaults
+        t0 = _events_ms(lambda: gr.gr_batch_run(b0), args.steps)
+        assert gr.gr_batch_status(b0)[0] == 0
+        gr.gr_batch_destroy(b0)
+        by_handle = {G.handle: G for G in Gs}
+        best_opts, _, chosen = tune.tune_batch_strategy(jobs, by_handle, reps=2)
         b = gr.gr_batch_create(jobs, gr.batch_opts(**best_opts))
         ts = _events_ms(lambda: gr.gr_batch_run(b), args.steps)
         assert gr.gr_batch_status(b)[0] == 0
@@ -654,8 +659,11 @@ def run_other(args):
               "ms_per_step": ms, "higher_is_better": True,
               "config": {"workload": "512 BFS/SSSP jobs (50/50) over 64 R-MAT graphs, scale "
                                      "U{10..18}, ef U{8..32}, weights U[1,64]; one persistent "
-                                     "launch replayed from a CUDA graph",
-                         "batch_opts": best_opts, "info": gr.gr_batch_info(b)},
+                                     "launch replayed from a CUDA graph; launch shape and "
+                                     "per-level strategy from the batch autotuner",
+                         "batch_opts": best_opts, "tuned": chosen, "info": gr.gr_batch_info(b)},
+              "library_defaults": {"ms": statistics.median(t0),
+                                   "jobs_per_s": 512 / statistics.median(t0) * 1e3},
               "plain_path": {"ms": mp, "jobs_per_s": 512 / mp * 1e3},
               "speedup_vs_plain": mp / ms})
         gr.gr_batch_destroy(b)

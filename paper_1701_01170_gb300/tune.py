@@ -196,6 +196,87 @@ def tune_batch(jobs, reps: int = 3, clusters=None, per_sm=(0,)) -> tuple[dict, f
     return best
 
 
+BATCH_BFS_BIG = [64, 256, 1024]
+BATCH_BFS_DO = [(0.01, 0.01), (0.05, 0.05), (0.2, 0.05)]
+BATCH_SSSP_BIG = [256, 1024, 4096]
+BATCH_DELTA_FACTORS = [0.5, 1.0, 2.0]
+
+
+def tune_batch_strategy(jobs, graphs_by_handle=None, reps: int = 3):
+    """Choose the batch's launch shape and per-level strategy by measuring the batch itself.
+
+    Coordinate search, each candidate timed as a whole batch launch: the cluster size (CTAs
+    per job), then for the BFS jobs the split threshold (warp batches vs grid-shared edge
+    chunks) and the push/pull switch factors (Eq. 5-6), then for the SSSP jobs the split
+    threshold and the near/far bucket width (a factor on each graph's default; needs
+    `graphs_by_handle`).  The jobs are updated in place with the winners; returns
+    (batch opts, ms per launch, chosen settings).  Results do not depend on any of these.
+    """
+    opts, best_ms = tune_batch(jobs, reps=reps)
+    chosen = {"cluster_size": opts["cluster_size"]}
+
+    def measure():
+        b = gr_batch_create(jobs, batch_opts(**opts))
+        ms = _time(lambda: gr_batch_run(b), reps, warm=1)
+        st, _ = gr_batch_status(b)
+        gr_batch_destroy(b)
+        if st != 0:
+            raise RuntimeError(f"batch failed while tuning (status {st})")
+        return ms
+
+    def search(name, values, apply):
+        nonlocal best_ms
+        best_v = None
+        for v in values:
+            apply(v)
+            ms = measure()
+            if ms < best_ms:
+                best_ms, best_v = ms, v
+        if best_v is not None:
+            apply(best_v)
+            chosen[name] = best_v
+        else:
+            apply(None)
+
+    bfs = [j for j in jobs if j.op == GR_OP_BFS]
+    sssp = [j for j in jobs if j.op == GR_OP_SSSP]
+    saved_bfs = [(j.big_degree, j.do_a, j.do_b) for j in bfs]
+    saved_sssp = [(j.big_degree, j.delta) for j in sssp]
+
+    def set_bfs_big(v):
+        for j, sv in zip(bfs, saved_bfs):
+            j.big_degree = sv[0] if v is None else v
+
+    def set_bfs_do(v):
+        for j, sv in zip(bfs, saved_bfs):
+            j.do_a, j.do_b = (sv[1], sv[2]) if v is None else v
+
+    def set_sssp_big(v):
+        for j, sv in zip(sssp, saved_sssp):
+            j.big_degree = sv[0] if v is None else v
+
+    base_delta = {}
+    if graphs_by_handle:
+        for j in sssp:
+            if j.g not in base_delta:
+                base_delta[j.g] = default_delta(graphs_by_handle[j.g])
+
+    def set_delta(v):
+        for j, sv in zip(sssp, saved_sssp):
+            j.delta = sv[1] if v is None else max(1, int(base_delta[j.g] * v))
+
+    if bfs:
+        search("bfs_big_degree", BATCH_BFS_BIG, set_bfs_big)
+        saved_bfs = [(j.big_degree, j.do_a, j.do_b) for j in bfs]
+        search("bfs_do", BATCH_BFS_DO, set_bfs_do)
+    if sssp:
+        search("sssp_big_degree", BATCH_SSSP_BIG, set_sssp_big)
+        saved_sssp = [(j.big_degree, j.delta) for j in sssp]
+        if base_delta:
+            search("sssp_delta_factor", BATCH_DELTA_FACTORS, set_delta)
+    return opts, best_ms, chosen
+
+
 def tune_jobs(jobs, graphs_by_handle, sample_sources: int = 2, cache: TuneCache | None = None):
     """Fill each job's per-level knobs from the tuned choice of its graph.
 

@@ -99,6 +99,28 @@ def test_batch_matches_single_queries(gr, cluster, use_graph):
         h.close()
 
 
+def test_tuned_batch_matches_single_queries(gr):
+    # the strategy tuner rewrites the jobs' knobs and the launch shape; the
+    # results must not move
+    from paper_1701_01170_gb300 import tune
+    graphs, triples = small_mix()
+    handles, jobs, outs = make_jobs(gr, graphs, triples)
+    by_handle = {h.handle: h for h in handles}
+    opts, ms, chosen = tune.tune_batch_strategy(jobs, by_handle, reps=1)
+    assert ms > 0 and chosen["cluster_size"] in tune.BATCH_CLUSTERS
+    for o, p in outs:
+        o.fill_(-5)
+        p.fill_(-5)
+    b = gr.gr_batch_create(jobs, gr.batch_opts(**opts))
+    gr.gr_batch_run(b)
+    st, _ = gr.gr_batch_status(b, len(jobs))
+    assert st == 0
+    check(graphs, triples, outs)
+    gr.gr_batch_destroy(b)
+    for h in handles:
+        h.close()
+
+
 def test_batch_rejects_bad_jobs(gr):
     import torch
     g = gg.rmat(8, 4, seed=1)
