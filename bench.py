@@ -686,11 +686,14 @@ def run_serve(args, gr, base):
     from paper_1701_01170_gb300 import serve
     graphs = {name: gr.Graph.from_csr(g) for name, g in wl.serving_graphs()}
     cands = {name: np.flatnonzero(np.diff(G.R.cpu().numpy()) > 0) for name, G in graphs.items()}
+    # BFS requests on the low-diameter R-MAT graphs are grouped into bit-parallel
+    # multi-source units (a few levels, each O(n)); the grids' thousands of levels make
+    # that O(n x levels), so their queries run alone on capped grids side by side
     multi = [n for n in graphs if n.startswith("rmat")]
     lanes = 4
     be = serve.GpuBackend(graphs, lanes, blocks_per_sm=1)
     be.prepare_multi(multi)
-    caps = be.calibrate([n for n in graphs if n not in multi],
+    caps = be.calibrate([n for n in graphs if not n.startswith("rmat")],
                         {n: int(cands[n][0]) for n in graphs})
     budget = 96 << 30     # per-lane workspaces; the graphs themselves take about 9 GB
     names = sorted(graphs)
@@ -713,7 +716,8 @@ def run_serve(args, gr, base):
           "config": {"workload": "serving: 8 resident graphs (R-MAT s18/20/22/24 ef16, grids "
                                  "1024^2..8192^2), Poisson BFS/SSSP 50/50, random sources, "
                                  f"{args.requests} requests per rate, {lanes} lanes, "
-                                 "96 GB workspace budget", "cta_caps": caps},
+                                 "96 GB workspace budget, R-MAT BFS grouped into "
+                                 "multi-source units", "cta_caps": caps},
           "per_rate": results})
 
 

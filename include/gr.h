@@ -331,6 +331,11 @@ typedef struct gr_msbfs_opts {
                          GR_SYMMETRIC graph)                                   */
   float push_ratio;   /* AUTO: pull once the active vertices' degree sum
                          exceeds push_ratio * m                              */
+  int32_t snapshot_levels; /* levels kept as per-level visit snapshots (depths
+                         then written in one coalesced pass); a traversal
+                         deeper than this writes later depths directly as
+                         bits appear, with two snapshots in ping-pong.  0 =
+                         as many as fit in 2 GB (at least 2)              */
 } gr_msbfs_opts;
 
 void gr_msbfs_opts_default(gr_msbfs_opts* o);
@@ -343,8 +348,9 @@ void gr_msbfs_opts_default(gr_msbfs_opts* o);
  * depth of v from srcs[i] (-1 if unreachable), exactly as gr_bfs would
  * report it.  Synchronous (the level loop reads one counter per level).  The
  * first call on a graph allocates the graph's multi-source scratch
- * (about 100 * n bytes), kept until gr_graph_destroy.  Calls on one graph
- * must not overlap.
+ * (about 100 * n bytes plus the snapshots: up to 2 GB, or two levels' worth
+ * when that is more), kept until gr_graph_destroy.  Calls on one graph must
+ * not overlap.
  */
 gr_status gr_bfs_multi(const gr_graph* g, const int32_t* srcs, int32_t k, int32_t* depth,
                        const gr_msbfs_opts* opts, void* stream);

@@ -60,7 +60,7 @@ class gr_sssp_state(ctypes.Structure):
 
 
 class gr_msbfs_opts(ctypes.Structure):
-    _fields_ = [("direction", c_i32), ("push_ratio", c_f32)]
+    _fields_ = [("direction", c_i32), ("push_ratio", c_f32), ("snapshot_levels", c_i32)]
 
 
 class gr_job(ctypes.Structure):

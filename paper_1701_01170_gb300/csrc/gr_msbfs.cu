@@ -34,8 +34,8 @@ struct GrMsState {
   u64* fcur;        // frontier words, n * 4
   u64* fnext;
   u64* acc;         // push accumulator / chunk accumulator, n * 4 (zero between levels)
-  u64* snap;        // snapshots, snap_cap levels of n * 4 words
-  int snap_cap;
+  u64* snap;        // snapshots: snap_bytes, levels of n * W words each
+  size_t snap_bytes;
   int32_t* active[2];
   int2* chunks;     // static (row, first edge) chunks of rows with degree >= big
   int nchunks;
@@ -50,6 +50,7 @@ namespace {
 constexpr int MS_T = 256;
 constexpr int MS_MAXW = 4;
 constexpr int MS_BIG = 1024;
+constexpr size_t MS_SNAP_BUDGET = (size_t)2 << 30;  // bytes of per-level snapshots at most
 
 struct MsArgs {
   int32_t n;
@@ -68,6 +69,9 @@ struct MsArgs {
   int nchunks;
   int big;
   u64 mask[MS_MAXW];
+  int32_t* depth;      // deep mode: depths written as bits appear (else NULL)
+  int64_t row_stride;
+  int32_t level_next;  // depth of the bits found in this level
 };
 
 template <int W>
@@ -120,6 +124,17 @@ __device__ __forceinline__ void ms_commit(const MsArgs& a, bool valid, int32_t v
     store_words<W>(a.snap_next + (size_t)v * W, nv);
     store_words<W>(a.fnext + (size_t)v * W, nw);
     if (any) degsum += (unsigned long long)deg;
+    if (any && a.depth) {  // deep mode: one depth per new source bit
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        u64 x = nw[w];
+        while (x) {
+          const int b = __ffsll((long long)x) - 1;
+          x &= x - 1ull;
+          a.depth[(int64_t)(w * 64 + b) * a.row_stride + v] = a.level_next;
+        }
+      }
+    }
   }
   unsigned mask = __ballot_sync(GR_FULL_MASK, any);
   if (mask) {
@@ -408,11 +423,13 @@ static gr_status ms_alloc(const gr_graph* g, GrMsState** out) {
   ms->big = MS_BIG;
   const size_t words = ((size_t)g->n + 1) * MS_MAXW;
   const int64_t chunk_cap = g->m / GR_CHUNK_EDGES + g->m / MS_BIG + 2;
-  ms->snap_cap = 16;
+  // room for 16 levels at the widest word count, within the snapshot budget,
+  // and never less than the two levels of deep mode
+  ms->snap_bytes = std::max<size_t>(2 * words * 8, std::min<size_t>(16 * words * 8, MS_SNAP_BUDGET));
   bool ok = cudaMalloc(&ms->fcur, words * 8) == cudaSuccess &&
             cudaMalloc(&ms->fnext, words * 8) == cudaSuccess &&
             cudaMalloc(&ms->acc, words * 8) == cudaSuccess &&
-            cudaMalloc(&ms->snap, words * 8 * ms->snap_cap) == cudaSuccess &&
+            cudaMalloc(&ms->snap, ms->snap_bytes) == cudaSuccess &&
             cudaMalloc(&ms->active[0], ((size_t)g->n + 1) * 4) == cudaSuccess &&
             cudaMalloc(&ms->active[1], ((size_t)g->n + 1) * 4) == cudaSuccess &&
             cudaMalloc(&ms->chunks, (size_t)chunk_cap * sizeof(int2)) == cudaSuccess &&
@@ -442,34 +459,35 @@ static gr_status ms_alloc(const gr_graph* g, GrMsState** out) {
   return GR_OK;
 }
 
-// Grow the snapshot buffer to hold at least `levels` levels (synchronous).
-static gr_status ms_grow_snap(GrMsState* ms, int levels, cudaStream_t s) {
-  if (levels <= ms->snap_cap) return GR_OK;
-  int cap = ms->snap_cap;
-  while (cap < levels) cap *= 2;
-  const size_t lvl_bytes = ((size_t)ms->n + 1) * MS_MAXW * 8;
+// Grow the snapshot buffer to at least `bytes` (synchronous), within
+// MS_SNAP_BUDGET; returns false if that is not possible.
+static bool ms_grow_snap(GrMsState* ms, size_t bytes, cudaStream_t s) {
+  if (bytes <= ms->snap_bytes) return true;
+  size_t cap = ms->snap_bytes;
+  while (cap < bytes) cap *= 2;
+  if (cap > MS_SNAP_BUDGET) cap = std::max(bytes, MS_SNAP_BUDGET);
+  if (cap > MS_SNAP_BUDGET) return false;
   u64* p = nullptr;
-  if (cudaMalloc(&p, lvl_bytes * cap) != cudaSuccess) {
+  if (cudaMalloc(&p, cap) != cudaSuccess) {
     (void)cudaGetLastError();
-    return GR_ERR_OOM;
+    return false;
   }
-  if (cudaMemcpyAsync(p, ms->snap, lvl_bytes * ms->snap_cap, cudaMemcpyDeviceToDevice, s) !=
-          cudaSuccess ||
+  if (cudaMemcpyAsync(p, ms->snap, ms->snap_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     (void)cudaGetLastError();
     cudaFree(p);
-    return GR_ERR_CUDA;
+    return false;
   }
   cudaFree(ms->snap);
   ms->snap = p;
-  ms->snap_cap = cap;
-  return GR_OK;
+  ms->snap_bytes = cap;
+  return true;
 }
 
 template <int W>
 static gr_status ms_run(const gr_graph* g, GrMsState* ms, const int32_t* srcs, int k,
                         int32_t* depth, int64_t row_stride, int direction, float push_ratio,
-                        cudaStream_t s) {
+                        int snapshot_levels, cudaStream_t s) {
   const int32_t n = g->n;
   // per-level snapshot stride uses W words per vertex
   const size_t lvl = (size_t)n * W;
@@ -502,13 +520,36 @@ static gr_status ms_run(const gr_graph* g, GrMsState* ms, const int32_t* srcs, i
   u64* fcur = ms->fcur;
   u64* fnext = ms->fnext;
   int level = 0;
+  // Snapshot mode keeps one visit snapshot per level and writes the depth
+  // matrix at the end in one coalesced pass; when the traversal outgrows the
+  // snapshot budget (or snapshot_levels) the depths found so far are written
+  // and later ones go straight to the matrix (deep mode), with two snapshot
+  // slots in ping-pong.
+  const int limit = snapshot_levels > 0 ? std::max(2, snapshot_levels) : INT_MAX;
+  bool deep = false;
+  int cur_slot = 0, next_slot = 1;
   while (nactive > 0) {
-    gr_status st = ms_grow_snap(ms, level + 2, s);
-    if (st != GR_OK) return st;
+    if (!deep) {
+      if (level + 2 <= limit && ms_grow_snap(ms, (size_t)(level + 2) * lvl * 8, s)) {
+        cur_slot = level;
+        next_slot = level + 1;
+      } else {
+        // levels 0..level are complete: write their depths, then go deep
+        ms_depth<W><<<std::min<int64_t>(((int64_t)n + 31) / 32, (int64_t)g->num_sms * 16), MS_T, 0,
+                       s>>>(n, ms->snap, level + 1, k, depth, row_stride);
+        if (cudaGetLastError() != cudaSuccess) return GR_ERR_CUDA;
+        deep = true;
+        cur_slot = level;
+        next_slot = level == 0 ? 1 : 0;
+      }
+    }
     a.fcur = fcur;
     a.fnext = fnext;
-    a.snap_cur = ms->snap + (size_t)level * lvl;
-    a.snap_next = ms->snap + (size_t)(level + 1) * lvl;
+    a.snap_cur = ms->snap + (size_t)cur_slot * lvl;
+    a.snap_next = ms->snap + (size_t)next_slot * lvl;
+    a.depth = deep ? depth : nullptr;
+    a.row_stride = row_stride;
+    a.level_next = level + 1;
     a.active = ms->active[level & 1];
     a.nactive = nactive;
     a.active_next = ms->active[(level + 1) & 1];
@@ -531,12 +572,15 @@ static gr_status ms_run(const gr_graph* g, GrMsState* ms, const int32_t* srcs, i
     nactive = (int)ms->h_ctl[0];
     degsum = ms->h_ctl[1];
     std::swap(fcur, fnext);
+    if (deep) std::swap(cur_slot, next_slot);
     ++level;
   }
-  // levels 0..level are valid snapshots (the last one adds nothing)
-  ms_depth<W><<<std::min<int64_t>(((int64_t)n + 31) / 32, (int64_t)g->num_sms * 16), MS_T, 0,
-                 s>>>(n, ms->snap, level + 1, k, depth, row_stride);
-  if (cudaGetLastError() != cudaSuccess) return GR_ERR_CUDA;
+  if (!deep) {
+    // levels 0..level are valid snapshots (the last one adds nothing)
+    ms_depth<W><<<std::min<int64_t>(((int64_t)n + 31) / 32, (int64_t)g->num_sms * 16), MS_T, 0,
+                   s>>>(n, ms->snap, level + 1, k, depth, row_stride);
+    if (cudaGetLastError() != cudaSuccess) return GR_ERR_CUDA;
+  }
   return GR_OK;
 }
 
@@ -544,6 +588,7 @@ extern "C" void gr_msbfs_opts_default(gr_msbfs_opts* o) {
   if (!o) return;
   o->direction = GR_DIR_AUTO;
   o->push_ratio = 0.02f;
+  o->snapshot_levels = 0;
 }
 
 extern "C" gr_status gr_bfs_multi(const gr_graph* g, const int32_t* srcs, int32_t k,
@@ -554,7 +599,8 @@ extern "C" gr_status gr_bfs_multi(const gr_graph* g, const int32_t* srcs, int32_
   gr_msbfs_opts o;
   gr_msbfs_opts_default(&o);
   if (opts) o = *opts;
-  if (o.direction < GR_DIR_AUTO || o.direction > GR_DIR_PULL) return GR_ERR_INVALID_ARG;
+  if (o.direction < GR_DIR_AUTO || o.direction > GR_DIR_PULL || o.snapshot_levels < 0)
+    return GR_ERR_INVALID_ARG;
   if (k == 0) return GR_OK;
   gr_graph* gm = const_cast<gr_graph*>(g);
   if (!gm->ms) {
@@ -566,9 +612,15 @@ extern "C" gr_status gr_bfs_multi(const gr_graph* g, const int32_t* srcs, int32_
     const int kk = std::min(256, k - base);
     int32_t* out = depth + (int64_t)base * g->n;
     gr_status st;
-    if (kk <= 64) st = ms_run<1>(g, gm->ms, srcs + base, kk, out, g->n, o.direction, o.push_ratio, s);
-    else if (kk <= 128) st = ms_run<2>(g, gm->ms, srcs + base, kk, out, g->n, o.direction, o.push_ratio, s);
-    else st = ms_run<4>(g, gm->ms, srcs + base, kk, out, g->n, o.direction, o.push_ratio, s);
+    if (kk <= 64)
+      st = ms_run<1>(g, gm->ms, srcs + base, kk, out, g->n, o.direction, o.push_ratio,
+                     o.snapshot_levels, s);
+    else if (kk <= 128)
+      st = ms_run<2>(g, gm->ms, srcs + base, kk, out, g->n, o.direction, o.push_ratio,
+                     o.snapshot_levels, s);
+    else
+      st = ms_run<4>(g, gm->ms, srcs + base, kk, out, g->n, o.direction, o.push_ratio,
+                     o.snapshot_levels, s);
     if (st != GR_OK) return st;
   }
   return GR_OK;

@@ -152,12 +152,14 @@ class GpuBackend:
     MULTI_OUT_BYTES = 256 << 20
 
     def __init__(self, graphs: dict, lanes: int, blocks_per_sm: int = 1, bfs_opts=None,
-                 sssp_opts=None):
+                 sssp_opts=None, multi_out_bytes: int | None = None):
         import torch
 
         from . import (GR_OP_BFS, GR_OP_SSSP, bfs_opts as _bo, gr_graph_footprint,
                        sssp_opts as _so)
         self.torch = torch
+        if multi_out_bytes:
+            self.MULTI_OUT_BYTES = int(multi_out_bytes)
         self.graphs = graphs                     # name -> Graph
         self.streams = [torch.cuda.Stream() for _ in range(lanes)]
         self.ws = [dict() for _ in range(lanes)]

@@ -63,6 +63,23 @@ def test_switch_ratio_does_not_change_results(gr, s13, ratio):
                           oracle.bfs_multi(g.R, g.C, srcs))
 
 
+@pytest.mark.parametrize("keep", [2, 3, 5])
+def test_deep_mode_writes_depths_directly(gr, s13, keep):
+    # after `keep` snapshot levels the depths of later levels are written as
+    # their bits appear; the matrix must not change
+    g, G = s13
+    srcs = np.concatenate([[0, 0], gg.sources(g, 90, seed=11)])
+    got = run_multi(gr, G, srcs, snapshot_levels=keep)
+    assert np.array_equal(got, oracle.bfs_multi(g.R, g.C, srcs))
+    m = gg.grid(48, 0.1, seed=3)
+    M = gr.Graph.from_csr(m)
+    msrcs = np.array([0, m.n - 1, m.n // 2, 17, 17], np.int32)
+    for direction in (0, 1):
+        got = run_multi(gr, M, msrcs, snapshot_levels=keep, direction=direction)
+        assert np.array_equal(got, oracle.bfs_multi(m.R, m.C, msrcs))
+    M.close()
+
+
 def test_high_diameter_grid_grows_snapshots(gr):
     g = gg.grid(48, 0.1, seed=3)
     G = gr.Graph.from_csr(g)
