@@ -276,9 +276,9 @@ def profiled_traffic() -> dict:
     launches, from the committed ncu summaries under profiles/, for the kernel versions they
     were captured on; None for a kernel whose sources changed since (digest mismatch)."""
     from paper_1701_01170_gb300 import _build
-    cur = _build.source_digest()
     out = {}
     for kind in ("bfs", "sssp"):
+        cur = _build.source_digest(kind)
         path = os.path.join(ROOT, "profiles", f"{kind}_persistent_rmat_s22.md")
         out[kind] = None
         try:
@@ -288,7 +288,7 @@ def profiled_traffic() -> dict:
                     if line.startswith("- ") and ":" in line:
                         k, v = line[2:].split(":", 1)
                         fields[k.strip()] = v.strip().strip("`")
-            if fields.get("source_digest") == cur:
+            if fields.get("kernel_source_digest") == cur:
                 out[kind] = int(fields["traffic_bytes_per_launch"])
         except (OSError, KeyError, ValueError):
             pass
@@ -372,11 +372,28 @@ def run_ours(args):
     if st != gr.GR_OK:
         raise RuntimeError(f"timed steps failed: {gr.status_str(st)}")
 
-    # counters of one BFS and one SSSP launch per source kind for the roofline
-    gr.gr_bfs(G.handle, srcs[0], depth, bpred, stream=stream)
+    # counters of one BFS and one SSSP launch per source kind for the roofline, and the
+    # per-level trace of the hub queries (level_stats; untimed)
+    cap = 256
+    lv_b = torch.zeros(4 * cap, dtype=torch.int32, device=dev)
+    lv_s = torch.zeros(4 * cap, dtype=torch.int32, device=dev)
+    gr.gr_bfs(G.handle, srcs[0], depth, bpred,
+              gr.bfs_opts(level_stats=lv_b.data_ptr(), max_levels=cap), stream=stream)
     bst = gr.gr_last_run_stats(G.handle)
-    gr.gr_sssp(G.handle, srcs[0], dist_t, spred, stream=stream)
+    gr.gr_sssp(G.handle, srcs[0], dist_t, spred,
+               gr.sssp_opts(level_stats=lv_s.data_ptr(), max_levels=cap), stream=stream)
     sst = gr.gr_last_run_stats(G.handle)
+    reached_s = int((dist_t != -1).sum().item())
+    tb = lv_b.view(cap, 4)[:min(cap, bst["levels"])].cpu().tolist()
+    ts_ = lv_s.view(cap, 4)[:min(cap, sst["levels"])].cpu().tolist()
+    trace = {
+        "bfs_hub_levels": [{"frontier": r[0], "pull": r[1], "m_f": r[2], "start_us": r[3] / 1e3}
+                           for r in tb],
+        "sssp_hub_steps": [{"near_rows": r[0], "split": r[1], "far": r[2], "start_us": r[3] / 1e3}
+                           for r in ts_],
+        "sssp_hub_reexpansion": sst["vertices"] / max(1, reached_s),
+        "sssp_hub_edges_per_m": sst["edges"] / max(1, g.m),
+    }
     hub_bfs_ms, hub_sssp_ms = [], []
     for _ in range(3):
         flush.zero_()
@@ -435,6 +452,7 @@ def run_ours(args):
         "roofline": roof[dominant],
         "roofline_other": roof["bfs" if dominant == "sssp" else "sssp"],
         "clocks": clk,
+        "trace": trace,
         "gpu_launches": 2 * args.steps,
         "e2e": e2e,
     }

@@ -34,17 +34,30 @@ def sources() -> list[str]:
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def source_digest() -> str:
-    """Content hash of the CUDA sources and the C ABI header (identifies a kernel version)."""
+# the sources each persistent kernel is compiled from (besides gr.h, whose
+# declarations of other entry points do not enter the kernel's code)
+KERNEL_SOURCES = {
+    "bfs": ("gr_bfs.cu", "gr_bfs_body.cuh", "gr_internal.cuh"),
+    "sssp": ("gr_sssp.cu", "gr_sssp_body.cuh", "gr_internal.cuh"),
+}
+
+
+def source_digest(kernel: str | None = None) -> str:
+    """Content hash identifying a kernel version: of every CUDA source and the C ABI
+    header, or, for kernel "bfs" / "sssp", of the sources that kernel is built from."""
     import hashlib
     h = hashlib.sha256()
-    files = sorted(f for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh")))
+    if kernel is None:
+        files = sorted(f for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh")))
+    else:
+        files = sorted(KERNEL_SOURCES[kernel])
     for f in files:
         h.update(f.encode())
         with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(fh.read())
-    with open(os.path.join(INCLUDE, "gr.h"), "rb") as fh:
-        h.update(fh.read())
+    if kernel is None:
+        with open(os.path.join(INCLUDE, "gr.h"), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
