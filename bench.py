@@ -287,7 +287,10 @@ def profiled_traffic() -> dict:
                 for line in f:
                     if line.startswith("- ") and ":" in line:
                         k, v = line[2:].split(":", 1)
-                        fields[k.strip()] = v.strip().strip("`")
+                        v = v.strip()
+                        if v.startswith("`"):        # a `quoted` value, then a comment
+                            v = v[1:].split("`", 1)[0]
+                        fields[k.strip()] = v
             if fields.get("kernel_source_digest") == cur:
                 out[kind] = int(fields["traffic_bytes_per_launch"])
         except (OSError, KeyError, ValueError):
