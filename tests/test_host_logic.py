@@ -1,0 +1,69 @@
+"""Host-side logic that needs no GPU: the batch strategy search of the
+autotuner (against a fake batch whose launch time depends on the knobs) and
+the benchmark's reading of the committed ncu summaries."""
+import types
+
+import pytest
+
+
+class FakeJob:
+    def __init__(self, g, op):
+        self.g, self.op = g, op
+        self.big_degree, self.do_a, self.do_b, self.delta = 0, 0.0, 0.0, 0
+
+
+def test_batch_strategy_search_keeps_the_fastest_knobs(monkeypatch):
+    from paper_1701_01170_gb300 import GR_OP_BFS, GR_OP_SSSP, tune
+
+    jobs = [FakeJob("g1", GR_OP_BFS), FakeJob("g1", GR_OP_SSSP), FakeJob("g2", GR_OP_BFS)]
+    created = []
+
+    def cost(opts):
+        # cluster 4, BFS split 256, do (0.2, 0.05), SSSP split 1024, delta x0.5 are best
+        c = {1: 9.0, 2: 8.0, 4: 5.0, 8: 6.0}[opts["cluster_size"]]
+        for j in jobs:
+            if j.op == GR_OP_BFS:
+                c += {0: 3.0, 64: 2.0, 256: 1.0, 1024: 2.5}[j.big_degree]
+                c += {(0.0, 0.0): 2.0, (0.01, 0.01): 1.5, (0.05, 0.05): 1.2,
+                      (0.2, 0.05): 0.5}[(round(j.do_a, 2), round(j.do_b, 2))]
+            else:
+                c += {0: 3.0, 256: 2.0, 1024: 0.5, 4096: 1.0}[j.big_degree]
+                c += {0: 3.0, 50: 0.25, 100: 1.0, 200: 2.0}[j.delta]
+        return c
+
+    def fake_create(js, opts):
+        created.append(dict(cluster_size=opts.cluster_size))
+        return types.SimpleNamespace()
+
+    monkeypatch.setattr(tune, "gr_batch_create", fake_create)
+    monkeypatch.setattr(tune, "gr_batch_run", lambda b: None)
+    monkeypatch.setattr(tune, "gr_batch_status", lambda b: (0, []))
+    monkeypatch.setattr(tune, "gr_batch_destroy", lambda b: None)
+    monkeypatch.setattr(tune, "batch_opts", lambda **kw: types.SimpleNamespace(**kw))
+    monkeypatch.setattr(tune, "default_delta", lambda G: 100)
+    # a launch "takes" the cost of the knobs the jobs hold when it is timed
+    monkeypatch.setattr(tune, "_time", lambda fn, reps, warm=1: cost(
+        {"cluster_size": created[-1]["cluster_size"]}))
+    opts, ms, chosen = tune.tune_batch_strategy(jobs, {"g1": object(), "g2": object()}, reps=1)
+    assert opts["cluster_size"] == 4
+    assert chosen["bfs_big_degree"] == 256 and chosen["bfs_do"] == (0.2, 0.05)
+    assert chosen["sssp_big_degree"] == 1024 and chosen["sssp_delta_factor"] == 0.5
+    assert [j.big_degree for j in jobs] == [256, 1024, 256]
+    assert jobs[1].delta == 50 and (round(jobs[0].do_a, 2), round(jobs[0].do_b, 2)) == (0.2, 0.05)
+    assert ms == pytest.approx(cost({"cluster_size": 4}))
+
+
+def test_profiled_traffic_reads_matching_summaries(tmp_path, monkeypatch):
+    import bench
+    from paper_1701_01170_gb300 import _build
+
+    (tmp_path / "profiles").mkdir()
+    dig = {k: _build.source_digest(k) for k in ("bfs", "sssp")}
+    (tmp_path / "profiles" / "bfs_persistent_rmat_s22.md").write_text(
+        f"# x\n\n- kernel_source_digest: `{dig['bfs']}` (comment)\n"
+        "- traffic_bytes_per_launch: 1234\n")
+    (tmp_path / "profiles" / "sssp_persistent_rmat_s22.md").write_text(
+        "- kernel_source_digest: `0000000000000000`\n- traffic_bytes_per_launch: 99\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    got = bench.profiled_traffic()
+    assert got == {"bfs": 1234, "sssp": None}     # a stale summary gives no traffic
