@@ -42,9 +42,18 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_only(text: str) -> bytes:
+    """Source text without comments and blank lines (comments do not change a kernel)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln.strip()).encode()
+
+
 def source_digest(kernel: str | None = None) -> str:
     """Content hash identifying a kernel version: of every CUDA source and the C ABI
-    header, or, for kernel "bfs" / "sssp", of the sources that kernel is built from."""
+    header, or, for kernel "bfs" / "sssp", of the code (comments stripped) of the
+    sources that kernel is built from."""
     import hashlib
     h = hashlib.sha256()
     if kernel is None:
@@ -54,7 +63,8 @@ def source_digest(kernel: str | None = None) -> str:
     for f in files:
         h.update(f.encode())
         with open(os.path.join(CSRC, f), "rb") as fh:
-            h.update(fh.read())
+            data = fh.read()
+        h.update(_code_only(data.decode()) if kernel else data)
     if kernel is None:
         with open(os.path.join(INCLUDE, "gr.h"), "rb") as fh:
             h.update(fh.read())

@@ -7,16 +7,20 @@
 // barrier separates levels, so no level costs a launch or a device-to-host
 // copy.  Each level is either
 //   * push (Sec. 5.1): advance fused with the visit functor and the filter
-//     (LB_CULL-style fusion, Sec. 5.3) — the frontier queue is expanded
-//     warp-centrically (the warp scans its 32 rows' degrees and walks the
-//     concatenated edges 32 at a time), rows of degree >= big_degree arrive
-//     pre-split into 1024-edge chunks shared by the whole grid; a visited
-//     bitmap with atomicOr claims each vertex once, so the output frontier
-//     needs no separate dedup pass; or
+//     (LB_CULL-style fusion, Sec. 5.3) — the frontier arrives in three
+//     size classes (Sec. 5.1.2): rows of degree >= big_degree pre-split into
+//     256-edge chunks dealt out over every warp of the grid, medium rows 4
+//     per warp batch, short rows 32 per warp batch, each batch expanded
+//     warp-centrically (the warp scans its rows' degrees and walks the
+//     concatenated edges in 32-wide strips); a visited bitmap with atomicOr
+//     claims each vertex once, so the output frontier needs no separate
+//     dedup pass; or
 //   * pull (Sec. 5.1.4, Alg. 2 Reverse_Advance): every unvisited vertex scans
 //     its row for a member of the current frontier bitmap and stops at the
-//     first hit; the unvisited set is the complement of the visited bitmap,
-//     read one 32-vertex word per warp.
+//     first hit; the first pull level reads the complement of the visited
+//     bitmap (4 words of 32 candidates per warp batch), later consecutive
+//     pull levels the compacted unvisited list the previous one wrote.  A
+//     pull level records its output as a bitmap only.
 // The direction follows the paper's Eq. 5-6 (push -> pull when
 // m_f > m_u * do_a, pull -> push when m_f < m_u * do_b) with m_f and m_u
 // counted exactly: every discovered vertex adds its degree to m_f.

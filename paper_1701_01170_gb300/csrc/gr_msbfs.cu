@@ -14,11 +14,13 @@
 //     takes 32 consecutive rows, walks their concatenated edges in 32-wide
 //     strips (the warp-centric load balancing of the single-source kernel)
 //     and combines each row's lanes with a segmented OR scan in registers —
-//     no atomics.  Rows of degree >= big are cut into 1024-edge chunks that
-//     all warps share and reduce with one atomicOr per chunk.
-// visit[] after every level is kept (snapshot per level); a last pass turns
-// the snapshots into the k x n depth matrix, writing each source's row
-// with coalesced 128-byte stores.
+//     no atomics.  Rows of degree >= big are cut into GR_CHUNK_EDGES-edge
+//     chunks that all warps share and reduce with one atomicOr per chunk.
+// visit[] after every level is kept (snapshot per level, up to 2 GB); a last
+// pass turns the snapshots into the k x n depth matrix, writing each source's
+// row with coalesced 128-byte stores.  A deeper traversal writes the depths
+// found so far, then writes later depths directly as bits appear, keeping
+// two snapshots in ping-pong.
 #include <algorithm>
 #include <climits>
 #include <new>
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(MS_T) ms_finalize(MsArgs a) {
 
 // ---- pull ---------------------------------------------------------------
 
-// Long rows: one warp per 1024-edge chunk ORs its neighbours' frontier words
+// Long rows: one warp per edge chunk ORs its neighbours' frontier words
 // and merges the result into acc[row] with one atomicOr per word.
 template <int W>
 __global__ void __launch_bounds__(MS_T) ms_pull_chunks(MsArgs a) {
