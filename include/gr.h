@@ -27,7 +27,8 @@
  *    are recorded in a device status word of the workspace and reported by
  *    gr_sync_status().  The library never traps or asserts on the device.
  *  - Thread safety: a gr_graph is immutable after creation and may be shared
- *    by concurrent calls; a gr_workspace must be used by one call at a time
+ *    by concurrent calls (gr_bfs_multi, whose scratch is per graph, takes a
+ *    per-graph lock); a gr_workspace must be used by one call at a time
  *    (calls on different streams need different workspaces).
  */
 #ifndef GR_H_
@@ -349,8 +350,9 @@ void gr_msbfs_opts_default(gr_msbfs_opts* o);
  * report it.  Synchronous (the level loop reads one counter per level).  The
  * first call on a graph allocates the graph's multi-source scratch
  * (about 100 * n bytes plus the snapshots: up to 2 GB, or two levels' worth
- * when that is more), kept until gr_graph_destroy.  Calls on one graph must
- * not overlap.
+ * when that is more), kept until gr_graph_destroy.  Calls on one graph are
+ * serialised by the library (a second caller blocks until the first has
+ * returned); calls on different graphs run concurrently.
  */
 gr_status gr_bfs_multi(const gr_graph* g, const int32_t* srcs, int32_t k, int32_t* depth,
                        const gr_msbfs_opts* opts, void* stream);

@@ -354,13 +354,16 @@ extern "C" gr_status gr_graph_create_csr(int32_t n, int64_t m, const int32_t* ro
     return GR_ERR_INVALID_ARG;
   *out = nullptr;
   cudaStream_t s = (cudaStream_t)stream;
+  int device = 0, num_sms = 0;
+  GR_CUDA_TRY(cudaGetDevice(&device));
+  GR_CUDA_TRY(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device));
   gr_graph* g = new (std::nothrow) gr_graph();
   if (!g) return GR_ERR_OOM;
   g->n = n;
   g->m = m;
   g->flags = flags;
-  GR_CUDA_TRY(cudaGetDevice(&g->device));
-  GR_CUDA_TRY(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device));
+  g->device = device;
+  g->num_sms = num_sms;
   auto fail = [&](gr_status st) {
     for (void* p : g->owned)
       if (p) cudaFree(p);

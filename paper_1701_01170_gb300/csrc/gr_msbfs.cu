@@ -23,6 +23,8 @@
 // two snapshots in ping-pong.
 #include <algorithm>
 #include <climits>
+#include <cstdint>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -604,16 +606,21 @@ extern "C" gr_status gr_bfs_multi(const gr_graph* g, const int32_t* srcs, int32_
   if (o.direction < GR_DIR_AUTO || o.direction > GR_DIR_PULL || o.snapshot_levels < 0)
     return GR_ERR_INVALID_ARG;
   if (k == 0) return GR_OK;
+  // The multi-source scratch belongs to the graph, so calls on one graph run
+  // one at a time: a call holds its graph's lock (one of 64, picked by the
+  // handle's address) until its last kernel has finished with that scratch.
+  static std::mutex graph_locks[64];
+  std::lock_guard<std::mutex> hold(graph_locks[((uintptr_t)g >> 4) % 64]);
   gr_graph* gm = const_cast<gr_graph*>(g);
   if (!gm->ms) {
     gr_status st = ms_alloc(g, &gm->ms);
     if (st != GR_OK) return st;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  for (int base = 0; base < k; base += 256) {
+  gr_status st = GR_OK;
+  for (int base = 0; base < k && st == GR_OK; base += 256) {
     const int kk = std::min(256, k - base);
     int32_t* out = depth + (int64_t)base * g->n;
-    gr_status st;
     if (kk <= 64)
       st = ms_run<1>(g, gm->ms, srcs + base, kk, out, g->n, o.direction, o.push_ratio,
                      o.snapshot_levels, s);
@@ -623,7 +630,12 @@ extern "C" gr_status gr_bfs_multi(const gr_graph* g, const int32_t* srcs, int32_
     else
       st = ms_run<4>(g, gm->ms, srcs + base, kk, out, g->n, o.direction, o.push_ratio,
                      o.snapshot_levels, s);
-    if (st != GR_OK) return st;
   }
-  return GR_OK;
+  // kernels already queued still use the scratch (the depth pass reads the
+  // snapshots): let them finish before the lock goes, on errors too
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return GR_ERR_CUDA;
+  }
+  return st;
 }

@@ -461,6 +461,9 @@ extern "C" gr_status gr_advance(const gr_graph* g, const int32_t* in, int64_t in
   else fn = FN_RELAX;
   if (fn >= FN_BFS && ((mode & GR_V2E) || !state)) return GR_ERR_INVALID_ARG;
   if (fn == FN_RELAX && !g->W && g->m > 0) return GR_ERR_UNSUPPORTED;
+  if ((fn == FN_BFS || fn == FN_BFS_IDEM) && !((const gr_bfs_state*)state)->depth)
+    return GR_ERR_INVALID_ARG;
+  if (fn == FN_RELAX && !((const gr_sssp_state*)state)->key) return GR_ERR_INVALID_ARG;
 
   if (in_len == 0) {
     if (cudaMemsetAsync(out_len, 0, sizeof(int64_t), s) != cudaSuccess) return GR_ERR_CUDA;
@@ -485,12 +488,9 @@ extern "C" gr_status gr_advance(const gr_graph* g, const int32_t* in, int64_t in
   a.cap = out_cap; a.out_len = olen; a.status = ws->status;
   if (fn == FN_BFS || fn == FN_BFS_IDEM) {
     const gr_bfs_state* st = (const gr_bfs_state*)state;
-    if (!st->depth) return GR_ERR_INVALID_ARG;
     a.depth = st->depth; a.pred = st->pred; a.level = st->level;
   } else if (fn == FN_RELAX) {
-    const gr_sssp_state* st = (const gr_sssp_state*)state;
-    if (!st->key) return GR_ERR_INVALID_ARG;
-    a.key = (unsigned long long*)st->key;
+    a.key = (unsigned long long*)((const gr_sssp_state*)state)->key;
   }
   if (fn == FN_NONE_ORDERED || fn == FN_NONE_EDGES) {
     write_len_and_check<<<1, 1, 0, s>>>(ws->dev_len, olen, out_cap, ws->status);
@@ -504,9 +504,10 @@ extern "C" gr_status gr_advance(const gr_graph* g, const int32_t* in, int64_t in
     case FN_BFS_IDEM: adv_expand<FN_BFS_IDEM><<<blocks_persist, T, 0, s>>>(a); break;
     default: adv_expand<FN_RELAX><<<blocks_persist, T, 0, s>>>(a); break;
   }
-  GR_LAUNCH_CHECK();
+  // the temporary offsets are released on every path once the launches are queued
+  const bool launched = cudaGetLastError() == cudaSuccess;
   if (tmp_alloc && cudaFreeAsync(item_off, s) != cudaSuccess) return GR_ERR_CUDA;
-  return GR_OK;
+  return launched ? GR_OK : GR_ERR_CUDA;
 }
 
 extern "C" gr_status gr_filter(const gr_graph* g, const int32_t* in, int64_t in_len,

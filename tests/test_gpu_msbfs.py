@@ -4,7 +4,7 @@ Every depth row must equal the oracle's queue BFS from that source, bit for
 bit.  Cases cover word boundaries of the bit masks (64, 65, 128, 256, 257
 sources), duplicate sources, push-only and pull-only schedules, a directed
 graph, and a high-diameter grid whose level count forces the snapshot
-buffer to grow.
+buffer to grow; concurrent calls on one graph from several threads.
 """
 import numpy as np
 import pytest
@@ -100,6 +100,43 @@ def test_directed_graph_uses_push(gr):
     G = gr.Graph.from_csr(g, symmetric=False)
     srcs = np.arange(0, 100, 3, dtype=np.int32)
     assert np.array_equal(run_multi(gr, G, srcs), oracle.bfs_multi(g.R, g.C, srcs))
+
+
+def test_concurrent_calls_on_one_graph(gr, s13):
+    # the multi-source scratch is per graph: calls from several host threads
+    # on their own streams must be serialised by the library, each one
+    # returning its own sources' depths
+    import threading
+
+    import torch
+    g, G = s13
+    sets = [gg.sources(g, k, seed=40 + i) for i, k in enumerate((5, 64, 70, 200))]
+    want = [oracle.bfs_multi(g.R, g.C, srcs) for srcs in sets]
+    got = [None] * len(sets)
+    errors = []
+
+    def worker(i):
+        try:
+            stream = torch.cuda.Stream()
+            ok = True
+            with torch.cuda.stream(stream):
+                depth = torch.empty(len(sets[i]) * G.n, dtype=torch.int32, device="cuda")
+                for _ in range(3):
+                    depth.fill_(-7)
+                    gr.gr_bfs_multi(G.handle, sets[i], depth, None, stream)
+                    h = host(depth).reshape(len(sets[i]), G.n)
+                    ok = ok and np.array_equal(h, want[i])
+            got[i] = ok
+        except Exception as e:  # reported below, on the test's thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=worker, args=(i,)) for i in range(len(sets))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    assert got == [True] * len(sets)
 
 
 def test_rejects_bad_sources(gr, s13):
