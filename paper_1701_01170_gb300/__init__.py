@@ -136,11 +136,13 @@ def load(build_if_missing: bool = False):
             raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build()")
         _build.build()
     lib = ctypes.CDLL(path)
+    missing = [name for name in _SIGNATURES if not hasattr(lib, name)]
+    if missing:
+        raise RuntimeError(f"{path} does not export {', '.join(missing)}: rebuild it")
     for name, (args, res) in _SIGNATURES.items():
-        if hasattr(lib, name):
-            f = getattr(lib, name)
-            f.argtypes = args
-            f.restype = res
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
     _lib = lib
     return lib
 
@@ -165,6 +167,28 @@ def _ptr(t):
     if not t.is_contiguous():
         raise ValueError("expected a contiguous tensor")
     return c_vp(t.data_ptr())
+
+
+def _buf32(t, count: int, what: str):
+    """Device pointer of a 4-byte-element CUDA tensor holding at least `count` elements.
+
+    The kernels write `count` 32-bit values through the pointer, so a smaller
+    or narrower tensor is rejected here instead of being overrun on the
+    device.  An int (a raw device address) is passed through unchecked.
+    """
+    if t is None or isinstance(t, int):
+        return _ptr(t)
+    if t.element_size() != 4:
+        raise ValueError(f"{what}: expected a 32-bit tensor, got {t.dtype}")
+    if t.numel() < count:
+        raise ValueError(f"{what}: needs {count} elements, the tensor has {t.numel()}")
+    return _ptr(t)
+
+
+def _graph_n(g) -> int:
+    n = c_i32()
+    _check(load().gr_graph_info(c_vp(g), ctypes.byref(n), None, None, None), "gr_graph_info")
+    return n.value
 
 
 def _stream(stream):
@@ -252,63 +276,56 @@ def gr_filter(g, inp, in_len, out, out_len, mode=GR_FILTER_EXACT_UNIQUE, state=N
     _check(st, "gr_filter")
 
 
-def bfs_opts(**kw) -> gr_bfs_opts:
-    o = gr_bfs_opts()
-    load().gr_bfs_opts_default(ctypes.byref(o))
-    names = {f[0] for f in gr_bfs_opts._fields_}
+def _opts(struct, default_fn: str, kw):
+    """The library's defaults for `struct`, then the given fields (unknown names raise)."""
+    o = struct()
+    getattr(load(), default_fn)(ctypes.byref(o))
+    names = {f[0] for f in struct._fields_}
     for k, v in kw.items():
         if k not in names:
-            raise TypeError(f"gr_bfs_opts has no field {k!r}")
+            raise TypeError(f"{struct.__name__} has no field {k!r}")
         setattr(o, k, v)
     return o
+
+
+def bfs_opts(**kw) -> gr_bfs_opts:
+    return _opts(gr_bfs_opts, "gr_bfs_opts_default", kw)
 
 
 def sssp_opts(**kw) -> gr_sssp_opts:
-    o = gr_sssp_opts()
-    load().gr_sssp_opts_default(ctypes.byref(o))
-    names = {f[0] for f in gr_sssp_opts._fields_}
-    for k, v in kw.items():
-        if k not in names:
-            raise TypeError(f"gr_sssp_opts has no field {k!r}")
-        setattr(o, k, v)
-    return o
+    return _opts(gr_sssp_opts, "gr_sssp_opts_default", kw)
 
 
 def gr_bfs(g, src, depth, pred=None, opts=None, stream=None):
-    st = load().gr_bfs(c_vp(g), src, _ptr(depth), _ptr(pred),
+    n = _graph_n(g)
+    st = load().gr_bfs(c_vp(g), src, _buf32(depth, n, "depth"), _buf32(pred, n, "pred"),
                        ctypes.byref(opts) if opts is not None else None, _stream(stream))
     _check(st, "gr_bfs")
 
 
 def gr_sssp(g, src, dist, pred=None, opts=None, stream=None):
-    st = load().gr_sssp(c_vp(g), src, _ptr(dist), _ptr(pred),
+    n = _graph_n(g)
+    st = load().gr_sssp(c_vp(g), src, _buf32(dist, n, "dist"), _buf32(pred, n, "pred"),
                         ctypes.byref(opts) if opts is not None else None, _stream(stream))
     _check(st, "gr_sssp")
 
 
 def msbfs_opts(**kw) -> gr_msbfs_opts:
-    o = gr_msbfs_opts()
-    load().gr_msbfs_opts_default(ctypes.byref(o))
-    for k, v in kw.items():
-        setattr(o, k, v)
-    return o
+    return _opts(gr_msbfs_opts, "gr_msbfs_opts_default", kw)
 
 
 def gr_bfs_multi(g, srcs, depth, opts=None, stream=None):
     """k-source bit-parallel BFS; srcs is a host int sequence, depth a CUDA int32 (k*n) tensor."""
     import numpy as np
     s = np.ascontiguousarray(srcs, dtype=np.int32)
-    st = load().gr_bfs_multi(c_vp(g), s.ctypes.data_as(c_vp), len(s), _ptr(depth),
+    depth_p = _buf32(depth, len(s) * _graph_n(g), "depth")
+    st = load().gr_bfs_multi(c_vp(g), s.ctypes.data_as(c_vp), len(s), depth_p,
                              ctypes.byref(opts) if opts is not None else None, _stream(stream))
     _check(st, "gr_bfs_multi")
 
 
 def batch_opts(**kw) -> gr_batch_opts:
-    o = gr_batch_opts()
-    load().gr_batch_opts_default(ctypes.byref(o))
-    for k, v in kw.items():
-        setattr(o, k, v)
-    return o
+    return _opts(gr_batch_opts, "gr_batch_opts_default", kw)
 
 
 def gr_batch_create(jobs, opts=None):

@@ -108,3 +108,47 @@ def test_ctypes_mirrors_match_the_compiled_header(tmp_path):
         assert int(got[name]) == ctypes.sizeof(st), name
         for f in st._fields_:
             assert int(got[f"{name}.{f[0]}"]) == getattr(st, f[0]).offset, (name, f[0])
+
+
+def test_binding_rejects_narrow_or_short_output_tensors():
+    # the kernels write n 32-bit values through each output pointer: the
+    # binding refuses tensors that would be overrun, before any GPU call
+    import torch
+
+    import paper_1701_01170_gb300 as gr
+    with pytest.raises(ValueError, match="32-bit"):
+        gr._buf32(torch.zeros(10, dtype=torch.int16), 10, "depth")
+    with pytest.raises(ValueError, match="32-bit"):
+        gr._buf32(torch.zeros(10, dtype=torch.int64), 10, "depth")
+    with pytest.raises(ValueError, match="needs 10 elements"):
+        gr._buf32(torch.zeros(9, dtype=torch.int32), 10, "dist")
+    with pytest.raises(ValueError, match="CUDA"):        # right size, but host memory
+        gr._buf32(torch.zeros(10, dtype=torch.int32), 10, "pred")
+    assert gr._buf32(None, 10, "pred") is None           # optional outputs stay optional
+
+
+def test_option_builders_reject_unknown_fields(lib_path):
+    import paper_1701_01170_gb300 as gr
+    for build in (gr.bfs_opts, gr.sssp_opts, gr.msbfs_opts, gr.batch_opts):
+        with pytest.raises(TypeError, match="no field"):
+            build(no_such_field=1)
+    assert gr.msbfs_opts(snapshot_levels=3).snapshot_levels == 3
+    assert gr.batch_opts(cluster_size=4).cluster_size == 4
+
+
+def test_load_refuses_a_library_missing_declared_symbols(tmp_path, monkeypatch):
+    # an out-of-date or foreign libgr.so must not load with some entry points unbound
+    import shutil
+
+    import paper_1701_01170_gb300 as gr
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "stub.c"
+    src.write_text("int gr_version(void) { return 1 << 16; }\n")
+    so = tmp_path / "libstub.so"
+    subprocess.check_call([cc, "-shared", "-fPIC", str(src), "-o", str(so)])
+    monkeypatch.setattr(gr, "_lib", None)
+    monkeypatch.setenv("GR_LIBRARY", str(so))
+    with pytest.raises(RuntimeError, match="does not export"):
+        gr.load()
