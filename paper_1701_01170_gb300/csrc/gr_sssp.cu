@@ -56,8 +56,8 @@ extern "C" void gr_sssp_opts_default(gr_sssp_opts* o) {
   o->max_blocks = 0;
 }
 
-// Bucket width from the graph: about one warp's worth of average edges
-// (warp size * mean weight / mean degree), at least 1.
+// Bucket width from the graph: 256 * mean weight / mean degree, at least 1
+// (wide buckets: a few repeated relaxations for far fewer grid-wide steps).
 static uint32_t default_delta(const gr_graph* g) { return gr_default_delta(g); }
 
 extern "C" gr_status gr_sssp(const gr_graph* g, int32_t src, uint32_t* dist, int32_t* pred,
