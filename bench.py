@@ -256,7 +256,7 @@ def run_reference(args):
 # -------------------------------------------------------------- GPU arm ---
 
 def algorithmic_bytes(kind, st, n):
-    """Bytes one launch must move for the work it did (per-unit figures in the design doc).
+    """Bytes one launch must move for the work it did, from these per-unit figures:
 
     BFS:  4 B per column read, 12 B per row opened (queue entry + R[u], R[u+1]),
           12 B per discovered vertex (depth, pred, next-queue entry),
