@@ -25,12 +25,16 @@
 
 namespace {
 
-// 20 warps per CTA, one CTA per SM: the register file then allows 96
-// registers a thread, which this kernel fits without spilling.  On the
-// R-MAT s22 workload an SSSP took 3.4 % less time than with 16 warps at 126
-// registers (more gathers in flight) and 6 % less than with 24 warps at 80
-// registers, which spill.
-constexpr int NT = 640;
+// CTA width, one CTA per SM.  Graphs with long rows (scale-free) run 20
+// warps: the register file then allows 96 registers a thread, which this
+// kernel fits without spilling, and the extra warps keep more label gathers
+// in flight (on R-MAT s22 an SSSP took 3.4 % less time than with 16 warps
+// at 126 registers, and 6 % less than with 24 warps at 80 registers, which
+// spill).  Graphs whose rows are all short (meshes) run 16 warps: their
+// thousands of small steps are bound by barriers, which wider CTAs slow
+// (3 % on a 4096^2 grid).
+constexpr int NT_WIDE = 640;
+constexpr int NT_NARROW = 512;
 
 #ifndef GR_SSSP_MIN_BLOCKS
 #define GR_SSSP_MIN_BLOCKS 1
@@ -38,6 +42,7 @@ constexpr int NT = 640;
 #ifndef GR_SSSP_BIG_STAGE
 #define GR_SSSP_BIG_STAGE 1  // staging buffers in dynamic shared memory (else the static arena)
 #endif
+template <int NT>
 __global__ void __launch_bounds__(NT, GR_SSSP_MIN_BLOCKS) sssp_persistent(SsspArgs a) {
   GridScope sc{a.ctl, a.status, a.spin, (int64_t)blockIdx.x * NT + threadIdx.x,
                (int64_t)gridDim.x * NT, 0u};
@@ -109,15 +114,17 @@ extern "C" gr_status gr_sssp(const gr_graph* g, int32_t src, uint32_t* dist, int
   a.level_stats = o.level_stats;
   a.max_levels = o.max_levels;
 
+  const bool wide = g->max_degree >= GR_MEDIUM_DEGREE;
+  const void* kernel = wide ? (const void*)sssp_persistent<NT_WIDE>
+                            : (const void*)sssp_persistent<NT_NARROW>;
+  const int nt = wide ? NT_WIDE : NT_NARROW;
   const size_t smem = sizeof(GrStageBufs);  // the dynamic shared-memory limit is raised once
-  int blocks = gr_launch_blocks((const void*)sssp_persistent, NT, smem, g->num_sms,
-                                o.blocks_per_sm);
+  int blocks = gr_launch_blocks(kernel, nt, smem, g->num_sms, o.blocks_per_sm);
   if (blocks <= 0) return GR_ERR_CUDA;
   if (o.max_blocks > 0 && blocks > o.max_blocks) blocks = o.max_blocks;
   if (gr_reset_ctl(ws, s) != cudaSuccess) return GR_ERR_CUDA;
   void* args[] = {&a};
-  if (cudaLaunchCooperativeKernel((const void*)sssp_persistent, dim3(blocks), dim3(NT), args, smem,
-                                  s) != cudaSuccess) {
+  if (cudaLaunchCooperativeKernel(kernel, dim3(blocks), dim3(nt), args, smem, s) != cudaSuccess) {
     (void)cudaGetLastError();
     return GR_ERR_CUDA;
   }
