@@ -52,7 +52,7 @@ def parse_args():
                    help="skip the timed CPU-oracle sample (for profiler runs)")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     p.add_argument("--e2e-steps", type=int, default=10)
-    p.add_argument("--workload", choices=["s22", "s16", "grid", "msbfs", "batch", "serve"],
+    p.add_argument("--workload", choices=["s22", "s16", "grid", "msbfs", "batch", "serve", "ops"],
                    default="s22",
                    help="s22 (default, the headline workload) or one of the other configurations")
     p.add_argument("--rates", default="20,2000,5000,10000,20000,50000",
@@ -416,15 +416,7 @@ def run_ours(args):
         e2e = run_e2e(gr, g, srcs, args, dev, rank)
 
     # ---- roofline of the dominant kernel (measured live above)
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
-    hbm = peaks.get("hbm_gbs")
-    peak_note = "measured" if hbm else "fallback"
-    hbm = hbm or 6800.0
+    hbm, peak_note = hbm_peak()
     bfs_ms = statistics.median(hub_bfs_ms)
     sssp_ms = statistics.median(hub_sssp_ms)
     bfs_b = algorithmic_bytes("bfs", bst, n)
@@ -559,6 +551,29 @@ def run_e2e(gr, g, srcs, args, dev, rank):
                     "streams; ms_per_step = (last read-back end - first upload start) / steps"}
 
 
+def hbm_peak():
+    """(HBM GB/s, "measured" | "fallback"): the measured copy bandwidth of this GPU model, else
+    the fallback figure of an earlier GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm = json.load(f).get("hbm_gbs")
+    except (OSError, ValueError):
+        hbm = None
+    return (hbm, "measured") if hbm else (6800.0, "fallback")
+
+
+def ops_algorithmic_bytes(op, f, e, u):
+    """Bytes a standalone operator must move: f frontier rows, e edges expanded, u outputs.
+
+    advance (ordered, no functor): frontier 4 B + row bounds 8 B + per-row output offset
+    8 B written and read per row, columns 4 B and outputs 4 B per edge.
+    exact-unique and cull filters: 4 B read per input item, 4 B written per output item.
+    """
+    if op == "advance":
+        return 4 * f + 8 * f + 16 * f + 8 * e
+    return 4 * e + 4 * u
+
+
 # ------------------------------------------------ the other configurations ---
 
 def _events_ms(fn, reps, warm=2):
@@ -621,6 +636,63 @@ def run_other(args):
         emit({"metric": "GTEPS", "value": val, "unit": "GTEPS", **base,
               "ms_per_step": sum(r["ms_per_query"] for r in res.values()),
               "higher_is_better": True, "config": {"workload": desc}, "per_op": res})
+        return
+    if args.workload == "ops":
+        # the standalone operators on the BFS frontier after the first level from the hub of
+        # R-MAT s22: advance (prefix-sum placement, ordered) and the two deduplicating filters
+        g, srcs = workload(22)
+        G = gr.Graph.from_csr(g)
+        hub = srcs[0]
+        deg = g.degrees()
+        Fh = np.ascontiguousarray(g.C[g.R[hub]:g.R[hub + 1]])   # sorted, distinct rows
+        E = int(deg[Fh].sum())
+        in_f = np.zeros(g.n, bool)
+        in_f[Fh] = True
+        sel = np.repeat(in_f, deg)                              # edges of the frontier's rows
+        want = g.C[sel]                                         # rows ascending = frontier order
+        mark = np.zeros(g.n, bool)
+        mark[want] = True
+        U = int(mark.sum())
+        F = torch.from_numpy(Fh).cuda()
+        out = torch.empty(E, dtype=torch.int32, device="cuda")
+        ol = torch.zeros(1, dtype=torch.int64, device="cuda")
+        uo = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        ul = torch.zeros(1, dtype=torch.int64, device="cuda")
+        reps = max(3, args.steps)
+        res = {}
+        t = _events_ms(lambda: gr.gr_advance(G.handle, F, len(Fh), out, ol), reps)
+        if int(ol.item()) != E or not np.array_equal(out.cpu().numpy(), want):
+            raise RuntimeError("advance output differs from the concatenated rows")
+        res["advance"] = (t, ops_algorithmic_bytes("advance", len(Fh), E, E))
+        for name, mode in (("filter_exact_unique", gr.GR_FILTER_EXACT_UNIQUE),
+                           ("filter_cull", gr.GR_FILTER_CULL)):
+            t = _events_ms(lambda: gr.gr_filter(G.handle, out, E, uo, ul, mode=mode), reps)
+            got = uo[:int(ul.item())].cpu().numpy()
+            if len(got) != U or not mark[got].all() or len(np.unique(got)) != U:
+                raise RuntimeError(f"{name} output is not the {U} distinct neighbours")
+            res[name] = (t, ops_algorithmic_bytes("filter", len(Fh), E, U))
+        if G.sync_status() != 0:
+            raise RuntimeError("operator status")
+        hbm, peak_note = hbm_peak()
+        per_op = {}
+        for name, (t, b) in res.items():
+            ms = statistics.median(t)
+            per_op[name] = {"ms": ms, "algorithmic_bytes": b, "gbs": b / (ms / 1e3) / 1e9,
+                            "frac": b / (ms / 1e3) / 1e9 / hbm}
+        tot_b = sum(b for _, b in res.values())
+        tot_ms = sum(p["ms"] for p in per_op.values())
+        adv = per_op["advance"]
+        emit({"metric": "operator GB/s", "value": tot_b / (tot_ms / 1e3) / 1e9, "unit": "GB/s",
+              **base, "ms_per_step": tot_ms, "higher_is_better": True,
+              "config": {"workload": "rmat_s22_ef16_seed2: advance of the hub's 162,948-row "
+                                     "neighbourhood (84.7 M edges), then exact-unique and cull "
+                                     "filters of its output",
+                         "frontier_rows": len(Fh), "edges": E, "distinct": U,
+                         "l2": "inputs larger than L2 (339 MB advance output)"},
+              "roofline": {"bound": "hbm", "achieved": adv["gbs"], "peak": hbm, "unit": "GB/s",
+                           "frac": adv["frac"], "traffic": None, "peak_kind": peak_note,
+                           "kernel": "adv_expand (with adv_degree_tiles, scan_block_sums)"},
+              "per_op": per_op})
         return
     if args.workload == "msbfs":
         g = gg.rmat(20, 16, 1)

@@ -67,3 +67,19 @@ def test_profiled_traffic_reads_matching_summaries(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     got = bench.profiled_traffic()
     assert got == {"bfs": 1234, "sssp": None}     # a stale summary gives no traffic
+
+
+def test_operator_bytes_and_peak_fallback(tmp_path, monkeypatch):
+    import json
+
+    import bench
+    # advance: 4 B frontier + 8 B row bounds + 16 B offsets per row, 8 B per edge;
+    # filters: 4 B per input item and 4 B per output item
+    assert bench.ops_algorithmic_bytes("advance", 10, 100, 100) == 10 * 28 + 800
+    assert bench.ops_algorithmic_bytes("filter", 10, 100, 7) == 400 + 28
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.hbm_peak() == (6800.0, "fallback")          # no measured peaks file
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6794.1}))
+    assert bench.hbm_peak() == (6794.1, "measured")
+    (tmp_path / "MEASURED_PEAKS.json").write_text("not json")
+    assert bench.hbm_peak() == (6800.0, "fallback")
