@@ -83,3 +83,32 @@ def test_operator_bytes_and_peak_fallback(tmp_path, monkeypatch):
     assert bench.hbm_peak() == (6794.1, "measured")
     (tmp_path / "MEASURED_PEAKS.json").write_text("not json")
     assert bench.hbm_peak() == (6800.0, "fallback")
+
+
+def test_reference_arm_prints_the_contract_line():
+    # `--impl reference` times the CPU oracle (no GPU) and prints one JSON line with the
+    # same metric and config keys as the GPU arm, plus its own cpu_baseline and e2e
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--scale", "12",
+           "--steps", "2", "--warmup", "3"]
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "GTEPS" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 3
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert d["config"]["graph"]["n"] == 4096
+    # a non-zero rank of a multi-rank launch prints nothing and exits 0
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=root, env=env)
+    assert out.returncode == 0 and not [l for l in out.stdout.splitlines() if l.startswith("{")]
