@@ -256,3 +256,30 @@ def test_operators_compose_into_bfs(gr, rmat14):
     assert np.array_equal(host(depth), want)
     assert oracle.bfs_certificate(g.R, g.C, src, want, host(pred)) == 0
     torch.cuda.synchronize()
+
+
+@pytest.mark.slow
+def test_config_s22_hub_neighbourhood(gr):
+    # the operator workload the benchmark times: advance of the hub's 162,948 rows of
+    # R-MAT s22 (84.7 M edges), then both deduplicating filters of that output
+    g = gg.rmat_weighted(22, 16, 2, 1, 64)
+    G = gr.Graph.from_csr(g)
+    hub = gg.max_degree_vertex(g)
+    F = np.ascontiguousarray(g.C[g.R[hub]:g.R[hub + 1]])
+    want = oracle.advance(g.R, g.C, F)
+    out = empty_i32(len(want))
+    ol = len_tensor()
+    gr.gr_advance(G.handle, dev(F), len(F), out, ol)
+    assert G.sync_status() == 0
+    assert int(ol.item()) == len(want)
+    assert np.array_equal(host(out), want)
+    uniq = oracle.filter_unique(g.n, want)
+    uo = empty_i32(g.n)
+    gr.gr_filter(G.handle, out, len(want), uo, ol, mode=gr.GR_FILTER_EXACT_UNIQUE)
+    assert G.sync_status() == 0
+    assert np.array_equal(host(uo)[:int(ol.item())], uniq)
+    gr.gr_filter(G.handle, out, len(want), uo, ol, mode=gr.GR_FILTER_CULL)
+    assert G.sync_status() == 0
+    got = host(uo)[:int(ol.item())]
+    assert len(got) == len(uniq) and np.array_equal(np.sort(got), np.sort(uniq))
+    G.close()
