@@ -37,7 +37,7 @@ import numpy as np  # noqa: E402
 SCALE, EF, SEED, WLO, WHI = 22, 16, 2, 1, 64
 N_RANDOM_SOURCES = 64
 METRIC = "GTEPS"
-L2_FLUSH_BYTES = 512 << 20   # larger than the 126 MB L2
+L2_FLUSH_BYTES = 512 << 20   # larger than the 129 MB L2
 
 
 def parse_args():
