@@ -112,3 +112,22 @@ def test_reference_arm_prints_the_contract_line():
     env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
     out = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=root, env=env)
     assert out.returncode == 0 and not [l for l in out.stdout.splitlines() if l.startswith("{")]
+
+
+def test_kernel_digest_ignores_comments_but_not_code(tmp_path, monkeypatch):
+    # the ncu summaries are matched to a kernel by this digest: editing a comment must keep
+    # them valid, any code change must not
+    import shutil
+
+    from paper_1701_01170_gb300 import _build
+    src = tmp_path / "csrc"
+    shutil.copytree(_build.CSRC, src)
+    monkeypatch.setattr(_build, "CSRC", str(src))
+    before = {k: _build.source_digest(k) for k in ("bfs", "sssp")}
+    body = src / "gr_sssp_body.cuh"
+    text = body.read_text()
+    body.write_text("// a new comment line\n" + text.replace("{", "{  /* inline comment */", 1))
+    assert {k: _build.source_digest(k) for k in ("bfs", "sssp")} == before
+    body.write_text(text.replace("GR_BULK_MIN_ROWS 4096", "GR_BULK_MIN_ROWS 4097", 1))
+    after = {k: _build.source_digest(k) for k in ("bfs", "sssp")}
+    assert after["sssp"] != before["sssp"] and after["bfs"] == before["bfs"]
