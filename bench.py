@@ -413,7 +413,9 @@ def run_ours(args):
     # ---- e2e: host buffers through the C ABI, copies inside the timed region
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(gr, g, srcs, args, dev, rank)
+        if ws > 1:
+            torch.distributed.barrier()      # replicas start their e2e regions together
+        e2e = combine_e2e(run_e2e(gr, g, srcs, args, dev, rank), ws)
 
     # ---- roofline of the dominant kernel (measured live above)
     hbm, peak_note = hbm_peak()
@@ -539,7 +541,7 @@ def run_e2e(gr, g, srcs, args, dev, rank):
         G.close()
     if st != gr.GR_OK:
         raise RuntimeError(f"e2e failed: {gr.status_str(-st)}")
-    return {"value": edges / (ms / 1e3) / 1e9, "unit": "GTEPS",
+    return {"value": edges / (ms / 1e3) / 1e9, "unit": "GTEPS", "_ms": ms, "_edges": edges,
             "h2d_bytes_per_step": int(g.R.nbytes + g.C.nbytes + g.W.nbytes),
             "d2h_bytes_per_step": int(4 * n * 4), "steps": steps,
             "ms_per_step": ms / steps,
@@ -572,6 +574,20 @@ def ops_algorithmic_bytes(op, f, e, u):
     if op == "advance":
         return 4 * f + 8 * f + 16 * f + 8 * e
     return 4 * e + 4 * u
+
+
+def combine_e2e(e2e: dict, world: int) -> dict:
+    """Whole-job e2e figure from one rank's: traversed edges summed over ranks over the
+    longest rank's timed region; copied bytes per step summed over ranks.  With one rank
+    the figure is the rank's own."""
+    e2e = dict(e2e)
+    ms, edges = e2e.pop("_ms"), e2e.pop("_edges")
+    ms_max, edges_all = aggregate_ranks(ms, edges, world)
+    e2e["value"] = edges_all / (ms_max / 1e3) / 1e9
+    e2e["ms_per_step"] = ms_max / e2e["steps"]
+    e2e["h2d_bytes_per_step"] *= world
+    e2e["d2h_bytes_per_step"] *= world
+    return e2e
 
 
 # ------------------------------------------------ the other configurations ---
