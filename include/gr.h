@@ -301,8 +301,9 @@ typedef struct gr_sssp_opts {
                             (near rows, 1 if a SPLIT step, far-pile length,
                             start time in ns after the first step)          */
   int32_t max_levels;    /* capacity of level_stats in steps                  */
-  int32_t bulk_rows;     /* near frontiers of at least this many rows (an edge
-                            chunk of a split row counts as 8) are relaxed in
+  int32_t bulk_rows;     /* near frontiers of at least this many rows (a row
+                            of 32 or more edges counts as 4, an edge chunk of
+                            a split row as 8) are relaxed in
                             bulk: atomics without return values plus a
                             label-change bitmap, then one pass over the bitmap
                             builds the next piles; smaller ones enqueue per
