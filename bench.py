@@ -52,13 +52,17 @@ def parse_args():
                    help="skip the timed CPU-oracle sample (for profiler runs)")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     p.add_argument("--e2e-steps", type=int, default=10)
-    p.add_argument("--workload", choices=["s22", "s16", "grid", "msbfs", "batch", "serve", "ops"],
+    p.add_argument("--workload", choices=["s22", "s16", "grid", "msbfs", "batch", "serve", "ops",
+                                          "push"],
                    default="s22",
                    help="s22 (default, the headline workload) or one of the other configurations")
     p.add_argument("--rates", default="20,2000,5000,10000,20000,50000",
                    help="serve: Poisson arrival rates (requests/s); the first one is below "
                         "the service rate (unloaded latency), the others saturate it")
     p.add_argument("--requests", type=int, default=400, help="serve: requests per rate")
+    p.add_argument("--no-extras", action="store_true",
+                   help="s22: skip the push-only BFS, multi-source, batch and serving legs "
+                        "(for profiler runs)")
     return p.parse_args()
 
 
@@ -77,10 +81,24 @@ def config(g, args, n_gpus):
                     f"seeded random non-isolated vertices",
         "graph": {"n": g.n, "m_directed": g.m, "weights": f"uint32 U[{WLO},{WHI}]",
                   "csr": "int32 row offsets, int32 columns"},
-        "sources": 1 + N_RANDOM_SOURCES,
+        "sources": f"{1 + N_RANDOM_SOURCES} in a fixed list (the highest-degree vertex first); "
+                   f"timed step k of rank r runs list entry (7r + k) mod {1 + N_RANDOM_SOURCES}, "
+                   f"so rank 0 times the hub first; warm-up runs the last W entries; the "
+                   f"line's sources_timed lists them",
         "l2": "flushed between steps (512 MB write, untimed); CSR is 1.04 GB > L2",
         "parallelism": f"replicas x{n_gpus} (independent queries per GPU)",
     }
+
+
+def timed_sources(srcs, rank, steps):
+    """List entries the timed steps of `rank` run, in order (the hub first on rank 0)."""
+    k = rank_source_offset(rank)
+    return [srcs[(k + i) % len(srcs)] for i in range(steps)]
+
+
+def warmup_sources(srcs, warmup):
+    """Warm-up runs the last entries of the list, so the timed steps keep the hub."""
+    return [srcs[-1 - (i % len(srcs))] for i in range(warmup)]
 
 
 # ---------------------------------------------------------------- clocks ---
@@ -255,20 +273,27 @@ def run_reference(args):
 
 # -------------------------------------------------------------- GPU arm ---
 
-def algorithmic_bytes(kind, st, n):
-    """Bytes one launch must move for the work it did, from these per-unit figures:
+def algorithmic_bytes(kind, n, m_r=0, n_r=0, st=None):
+    """Bytes one launch must move for its query, by the per-unit figures of the method.
 
-    BFS:  4 B per column read, 12 B per row opened (queue entry + R[u], R[u+1]),
-          12 B per discovered vertex (depth, pred, next-queue entry),
-          8 B per vertex for the depth/pred initialisation.
-    SSSP: 8 B per column read (column + weight), 16 B per row opened
-          (queue entry, R pair, key[u]), 12 B per successful relaxation
-          (8 B key atomic + 4 B queue entry), 32 B per vertex (key and stamp
-          initialisation, key read and dist/pred write at unpack).
+    push_bfs: 4 B per column of a reached vertex (m_r: the sum of the degrees
+              of the reached vertices), 24 B per reached vertex (frontier entry
+              in and out, its two row offsets, its depth and pred writes), 8 B
+              per vertex for the depth/pred initialisation: 4 m_r + 24 n_r + 8 n.
+    bfs:      the direction-optimising launch counted from its own counters:
+              push rows as above, pull levels 4 B per neighbour checked and 12 B
+              per unvisited candidate (its row offsets and depth):
+              4 edges + 12 rows + 12 discovered + 8 n.
+    sssp:     the lower bound that relaxes every edge of a reached vertex once:
+              8 B per edge (column + weight) and 28 B per vertex (key and stamp
+              initialisation, key read and dist/pred write at unpack): 8 m_r + 28 n.
+              Repeated relaxations are reported beside it, not counted in it.
     """
+    if kind == "push_bfs":
+        return 4 * m_r + 24 * n_r + 8 * n
     if kind == "bfs":
         return 4 * st["edges"] + 12 * st["vertices"] + 12 * st["updates"] + 8 * n
-    return 8 * st["edges"] + 16 * st["vertices"] + 12 * st["updates"] + 32 * n
+    return 8 * m_r + 28 * n
 
 
 def profiled_traffic() -> dict:
@@ -277,9 +302,11 @@ def profiled_traffic() -> dict:
     were captured on; None for a kernel whose sources changed since (digest mismatch)."""
     from paper_1701_01170_gb300 import _build
     out = {}
-    for kind in ("bfs", "sssp"):
-        cur = _build.source_digest(kind)
-        path = os.path.join(ROOT, "profiles", f"{kind}_persistent_rmat_s22.md")
+    for kind, fname in (("bfs", "bfs_persistent_rmat_s22.md"),
+                        ("sssp", "sssp_persistent_rmat_s22.md"),
+                        ("push_bfs", "bfs_persistent_push_rmat_s22.md")):
+        cur = _build.source_digest("bfs" if kind == "push_bfs" else kind)
+        path = os.path.join(ROOT, "profiles", fname)
         out[kind] = None
         try:
             fields = {}
@@ -296,6 +323,13 @@ def profiled_traffic() -> dict:
         except (OSError, KeyError, ValueError):
             pass
     return out
+
+
+def roofline_entry(kernel, launch, byts, ms, hbm, peak_note, traffic, **extra):
+    ach = byts / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": traffic, "peak_kind": peak_note, "kernel": kernel, "launch": launch,
+            "algorithmic_bytes": byts, "launch_ms": ms, **extra}
 
 
 def run_ours(args):
@@ -322,85 +356,98 @@ def run_ours(args):
     spred = torch.empty_like(depth)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
+    # BFS and SSSP run on workspaces of their own, so that each launch's work counters can
+    # be read after the step
+    ws_bfs = gr.gr_workspace_create(G.handle, gr.GR_OP_BFS)
+    bopts = gr.bfs_opts(ws=ws_bfs)
+    sopts = gr.sssp_opts()
 
-    def query_edges():
-        eb = int((deg_t * (depth >= 0)).sum().item())
-        es = int((deg_t * (dist_t != -1)).sum().item())
-        return eb, es
+    def reached_stats(t, sssp):
+        r = (t != -1) if sssp else (t >= 0)
+        return int((deg_t * r).sum().item()), int(r.sum().item())
 
     def step(src, evs):
+        # the L2 flush runs on the GPU while the host prepares the first launch, so the
+        # start event does not time host launch overhead
+        flush.zero_()
         evs[0].record(stream)
-        gr.gr_bfs(G.handle, src, depth, bpred, stream=stream)
+        gr.gr_bfs(G.handle, src, depth, bpred, bopts, stream=stream)
         evs[1].record(stream)
-        gr.gr_sssp(G.handle, src, dist_t, spred, stream=stream)
+        gr.gr_sssp(G.handle, src, dist_t, spred, sopts, stream=stream)
         evs[2].record(stream)
 
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    k = rank_source_offset(rank)
-    for _ in range(args.warmup):
-        step(srcs[k % len(srcs)], evs)
-        k += 1
+    for src in warmup_sources(srcs, args.warmup):
+        step(src, evs)
     torch.cuda.synchronize()
     st = G.sync_status()
     if st != gr.GR_OK:
         raise RuntimeError(f"warm-up failed: {gr.status_str(st)}")
 
+    timed = timed_sources(srcs, rank, args.steps)
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     time.sleep(0.3)
     t_bfs, t_sssp, e_bfs, e_sssp = [], [], 0, 0
-    b_bytes, s_bytes = [], []
+    b_alg, s_alg = 0, 0            # algorithmic bytes of the timed launches
+    s_relaxed, s_rows, s_mr, s_nr = 0, 0, 0, 0
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    for _ in range(args.steps):
-        src = srcs[k % len(srcs)]
-        k += 1
+    for src in timed:
         step(src, evs)
         evs[2].synchronize()
         t_bfs.append(evs[0].elapsed_time(evs[1]))
         t_sssp.append(evs[1].elapsed_time(evs[2]))
-        # untimed: edge counts, kernel counters, status, L2 flush
-        eb, es = query_edges()
+        # untimed: edge counts, kernel counters (the next step's flush follows)
+        eb, _ = reached_stats(depth, False)
+        es, nrs = reached_stats(dist_t, True)
         e_bfs += eb
         e_sssp += es
-        flush.zero_()
+        bst = gr.gr_last_run_stats(G.handle, ws_bfs)
+        sst = gr.gr_last_run_stats(G.handle)
+        b_alg += algorithmic_bytes("bfs", n, st=bst)
+        s_alg += algorithmic_bytes("sssp", n, m_r=es, n_r=nrs)
+        s_relaxed += sst["edges"]
+        s_rows += sst["vertices"]
+        s_mr += es
+        s_nr += nrs
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
     st = G.sync_status()
-    if st != gr.GR_OK:
+    if st != gr.GR_OK or gr.gr_sync_status(G.handle, ws_bfs) != gr.GR_OK:
         raise RuntimeError(f"timed steps failed: {gr.status_str(st)}")
 
-    # counters of one BFS and one SSSP launch per source kind for the roofline, and the
-    # per-level trace of the hub queries (level_stats; untimed)
+    # the hub launches once more with per-level traces (untimed), then timed alone three
+    # times: the launch the committed ncu summaries capture
     cap = 256
     lv_b = torch.zeros(4 * cap, dtype=torch.int32, device=dev)
     lv_s = torch.zeros(4 * cap, dtype=torch.int32, device=dev)
-    gr.gr_bfs(G.handle, srcs[0], depth, bpred,
-              gr.bfs_opts(level_stats=lv_b.data_ptr(), max_levels=cap), stream=stream)
-    bst = gr.gr_last_run_stats(G.handle)
-    gr.gr_sssp(G.handle, srcs[0], dist_t, spred,
+    hub = srcs[0]
+    gr.gr_bfs(G.handle, hub, depth, bpred,
+              gr.bfs_opts(ws=ws_bfs, level_stats=lv_b.data_ptr(), max_levels=cap), stream=stream)
+    hub_bst = gr.gr_last_run_stats(G.handle, ws_bfs)
+    gr.gr_sssp(G.handle, hub, dist_t, spred,
                gr.sssp_opts(level_stats=lv_s.data_ptr(), max_levels=cap), stream=stream)
-    sst = gr.gr_last_run_stats(G.handle)
-    reached_s = int((dist_t != -1).sum().item())
-    tb = lv_b.view(cap, 4)[:min(cap, bst["levels"])].cpu().tolist()
-    ts_ = lv_s.view(cap, 4)[:min(cap, sst["levels"])].cpu().tolist()
+    hub_sst = gr.gr_last_run_stats(G.handle)
+    hub_ms_r, hub_n_r = reached_stats(dist_t, True)
+    tb = lv_b.view(cap, 4)[:min(cap, hub_bst["levels"])].cpu().tolist()
+    ts_ = lv_s.view(cap, 4)[:min(cap, hub_sst["levels"])].cpu().tolist()
     trace = {
         "bfs_hub_levels": [{"frontier": r[0], "pull": r[1], "m_f": r[2], "start_us": r[3] / 1e3}
                            for r in tb],
         "sssp_hub_steps": [{"near_rows": r[0], "split": r[1], "far": r[2], "start_us": r[3] / 1e3}
                            for r in ts_],
-        "sssp_hub_reexpansion": sst["vertices"] / max(1, reached_s),
-        "sssp_hub_edges_per_m": sst["edges"] / max(1, g.m),
+        "sssp_hub_rows_per_reached": hub_sst["vertices"] / max(1, hub_n_r),
+        "sssp_hub_edges_relaxed_per_m_r": hub_sst["edges"] / max(1, hub_ms_r),
     }
     hub_bfs_ms, hub_sssp_ms = [], []
     for _ in range(3):
-        flush.zero_()
-        step(srcs[0], evs)
+        step(hub, evs)
         evs[2].synchronize()
         hub_bfs_ms.append(evs[0].elapsed_time(evs[1]))
         hub_sssp_ms.append(evs[1].elapsed_time(evs[2]))
@@ -417,27 +464,35 @@ def run_ours(args):
             torch.distributed.barrier()      # replicas start their e2e regions together
         e2e = combine_e2e(run_e2e(gr, g, srcs, args, dev, rank), ws)
 
-    # ---- roofline of the dominant kernel (measured live above)
+    # ---- roofline: algorithmic bytes of the timed launches over their summed event time
     hbm, peak_note = hbm_peak()
-    bfs_ms = statistics.median(hub_bfs_ms)
-    sssp_ms = statistics.median(hub_sssp_ms)
-    bfs_b = algorithmic_bytes("bfs", bst, n)
-    sssp_b = algorithmic_bytes("sssp", sst, n)
-    dominant = "sssp" if sum(t_sssp) >= sum(t_bfs) else "bfs"
     traffic = profiled_traffic()
-    roof = {}
-    for kind, b, ms, stt in (("sssp", sssp_b, sssp_ms, sst), ("bfs", bfs_b, bfs_ms, bst)):
-        ach = b / (ms / 1e3) / 1e9
-        roof[kind] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                      "frac": ach / hbm, "traffic": traffic.get(kind), "peak_kind": peak_note,
-                      "kernel": f"{kind}_persistent", "launch": "hub source",
-                      "algorithmic_bytes": b, "launch_ms": ms, "counters": stt}
-
+    roof = {
+        "sssp": roofline_entry(
+            "sssp_persistent", f"mean over the {len(timed)} timed launches", s_alg / len(timed),
+            sum(t_sssp) / len(timed), hbm, peak_note, traffic.get("sssp"),
+            formula="8 m_r + 28 n (every edge of a reached vertex relaxed once)",
+            edges_relaxed_per_m_r=s_relaxed / max(1, s_mr),
+            rows_opened_per_reached=s_rows / max(1, s_nr),
+            hub={"algorithmic_bytes": algorithmic_bytes("sssp", n, m_r=hub_ms_r, n_r=hub_n_r),
+                 "ms": statistics.median(hub_sssp_ms), "counters": hub_sst,
+                 "m_r": hub_ms_r, "n_r": hub_n_r},
+            traffic_launch="hub source (ncu, one launch)"),
+        "bfs": roofline_entry(
+            "bfs_persistent", f"mean over the {len(timed)} timed launches", b_alg / len(timed),
+            sum(t_bfs) / len(timed), hbm, peak_note, traffic.get("bfs"),
+            formula="4 edges + 12 rows + 12 discovered + 8 n from the launch's counters",
+            hub={"algorithmic_bytes": algorithmic_bytes("bfs", n, st=hub_bst),
+                 "ms": statistics.median(hub_bfs_ms), "counters": hub_bst},
+            traffic_launch="hub source (ncu, one launch)"),
+    }
+    dominant = "sssp" if sum(t_sssp) >= sum(t_bfs) else "bfs"
     out = {
         "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic", "config": config(g, args, ws),
+        "sources_timed": timed,
         "breakdown": {"bfs_ms_mean": statistics.mean(t_bfs), "sssp_ms_mean": statistics.mean(t_sssp),
                       "bfs_gteps": e_bfs / (sum(t_bfs) / 1e3) / 1e9,
                       "sssp_gteps": e_sssp / (sum(t_sssp) / 1e3) / 1e9,
@@ -445,6 +500,8 @@ def run_ours(args):
                       "sssp_ms_median": statistics.median(t_sssp),
                       "bfs_ms_p99": float(np.percentile(t_bfs, 99)),
                       "sssp_ms_p99": float(np.percentile(t_sssp, 99)),
+                      "kernel_share": {"sssp_persistent": sum(t_sssp) / dev_ms,
+                                       "bfs_persistent": sum(t_bfs) / dev_ms},
                       "wall_s_timed_loop": wall},
         "roofline": roof[dominant],
         "roofline_other": roof["bfs" if dominant == "sssp" else "sssp"],
@@ -453,13 +510,85 @@ def run_ours(args):
         "gpu_launches": 2 * args.steps,
         "e2e": e2e,
     }
+    if rank == 0 and not args.no_extras:
+        out["push_bfs"] = measure_push_bfs(gr, G, g, timed, depth, flush, hbm, peak_note,
+                                           traffic.get("push_bfs"), deg_t, stream)
+    gr.gr_workspace_destroy(ws_bfs)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(g, srcs)
+    G.close()
+    del G
+    if rank == 0 and ws == 1 and not args.no_extras:
+        # the batched and served forms, each against the plain one-query path on this GPU
+        out["msbfs"] = measure_msbfs(gr, reps=3)
+        out["batch"] = measure_batch(gr, reps=5)
+        out["serve"] = measure_serve(gr, rates=[20.0, 2000.0], requests=160)
     if rank == 0:
         emit(out)
-    G.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def measure_push_bfs(gr, G, g, sources, do_depth, flush, hbm, peak_note, traffic, deg_t,
+                     stream):
+    """Push-only BFS (advance + visit + cull fused, no pull levels) from the same sources:
+    its HBM fraction against 4 m_r + 24 n_r + 8 n, the advance + filter figure of merit.
+    Depths must equal the direction-optimising run's."""
+    import torch
+    n = g.n
+    depth = torch.empty(n, dtype=torch.int32, device="cuda")
+    opts = gr.bfs_opts(direction=gr.GR_DIR_PUSH)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def once(src):
+        flush.zero_()
+        e0.record(stream)
+        gr.gr_bfs(G.handle, src, depth, None, opts, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    once(sources[0])
+    tot_ms, tot_b, tot_e, same = 0.0, 0, 0, True
+    per = []
+    hub_ms = []
+    for i, src in enumerate(sources):
+        ms = once(src)
+        r = depth >= 0
+        m_r, n_r = int((deg_t * r).sum().item()), int(r.sum().item())
+        b = algorithmic_bytes("push_bfs", n, m_r=m_r, n_r=n_r)
+        gr.gr_bfs(G.handle, src, do_depth, None, stream=stream)      # direction-optimising
+        same = same and bool(torch.equal(depth, do_depth))
+        tot_ms += ms
+        tot_b += b
+        tot_e += m_r
+        per.append(ms)
+        if i == 0:
+            hub_ms.append(ms)
+            hub_b = b
+    for _ in range(2):
+        hub_ms.append(once(sources[0]))
+    # per-level trace of the first source (untimed)
+    cap = 256
+    lv = torch.zeros(4 * cap, dtype=torch.int32, device="cuda")
+    gr.gr_bfs(G.handle, sources[0], depth, None,
+              gr.bfs_opts(direction=gr.GR_DIR_PUSH, level_stats=lv.data_ptr(), max_levels=cap),
+              stream=stream)
+    levels = gr.gr_last_run_stats(G.handle)["levels"]
+    trace = [{"frontier": r[0], "m_f": r[2], "start_us": r[3] / 1e3}
+             for r in lv.view(cap, 4)[:min(cap, levels)].cpu().tolist()]
+    if G.sync_status() != gr.GR_OK:
+        raise RuntimeError("push-only BFS failed")
+    hub = roofline_entry("bfs_persistent (push only)", "first timed source", hub_b,
+                         statistics.median(hub_ms), hbm, peak_note, traffic,
+                         formula="4 m_r + 24 n_r + 8 n")
+    return {"kernel": "bfs_persistent, direction = push only",
+            "formula": "4 m_r + 24 n_r + 8 n (m_r: sum of degrees of reached vertices)",
+            "sources": len(sources), "ms_mean": tot_ms / len(sources),
+            "ms_median": statistics.median(per), "gteps": tot_e / (tot_ms / 1e3) / 1e9,
+            "achieved": tot_b / (tot_ms / 1e3) / 1e9, "peak": hbm,
+            "frac": tot_b / (tot_ms / 1e3) / 1e9 / hbm, "first_source": hub,
+            "depths_identical_to_direction_optimising": same, "first_source_levels": trace}
 
 
 def run_e2e(gr, g, srcs, args, dev, rank):
@@ -710,75 +839,42 @@ def run_other(args):
                            "kernel": "adv_expand (with adv_degree_tiles, scan_block_sums)"},
               "per_op": per_op})
         return
-    if args.workload == "msbfs":
-        g = gg.rmat(20, 16, 1)
-        srcs = gg.sources(g, 256, seed=4)
+    if args.workload == "push":
+        # the push-only BFS leg of the s22 line on its own (hub first), for profiler runs
+        g, srcs = workload(22)
         G = gr.Graph.from_csr(g)
-        D = torch.empty(256 * g.n, dtype=torch.int32, device="cuda")
-        ts = _events_ms(lambda: gr.gr_bfs_multi(G.handle, srcs, D), args.steps)
-        deg = g.degrees()
-        Dh = D.view(256, g.n).cpu().numpy()
-        edges = int(sum(int(deg[row >= 0].sum()) for row in Dh))
+        hbm, peak_note = hbm_peak()
         d = torch.empty(g.n, dtype=torch.int32, device="cuda")
-
-        def plain():
-            for s_ in srcs:
-                gr.gr_bfs(G.handle, int(s_), d, None)
-        tp = _events_ms(plain, max(1, args.steps // 4), warm=1)
-        ms, mp = statistics.median(ts), statistics.median(tp)
-        emit({"metric": "GTEPS", "value": edges / (ms / 1e3) / 1e9, "unit": "GTEPS", **base,
-              "ms_per_step": ms, "higher_is_better": True,
-              "config": {"workload": "rmat_s20_ef16_seed1: 256-source bit-parallel BFS "
-                                     "(sources: 256 random non-isolated vertices, seed 4)"},
-              "plain_path": {"ms_256_gr_bfs": mp, "gteps": edges / (mp / 1e3) / 1e9},
-              "speedup_vs_plain": mp / ms})
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+        deg_t = torch.from_numpy(g.degrees().astype(np.int64)).cuda()
+        r = measure_push_bfs(gr, G, g, srcs[:max(1, args.steps)], d, flush, hbm, peak_note,
+                             profiled_traffic().get("push_bfs"), deg_t,
+                             torch.cuda.current_stream())
+        G.close()
+        emit({"metric": "GB/s", "value": r["achieved"], "unit": "GB/s", **base,
+              "ms_per_step": r["ms_mean"], "higher_is_better": True,
+              "config": {"workload": "rmat_s22_ef16_seed2: push-only BFS from the highest-degree "
+                                     "vertex, then the seeded random sources"},
+              "roofline": r["first_source"], **r})
+        return
+    if args.workload == "msbfs":
+        r = measure_msbfs(gr, reps=args.steps)
+        emit({"metric": "GTEPS", "value": r["gteps"], "unit": "GTEPS", **base,
+              "ms_per_step": r["ms"], "higher_is_better": True,
+              "config": {"workload": r["workload"]}, **r})
         return
     if args.workload == "batch":
-        from graphgen import workloads as wl
-        bgs = wl.batch_graphs(64, seed=5)
-        triples = wl.batch_jobs(bgs, 512, seed=5)
-        Gs = [gr.Graph.from_csr(b.csr) for b in bgs]
-        jobs, outs = [], []
-        for gi, op, src in triples:
-            o = torch.empty(Gs[gi].n, dtype=torch.int32, device="cuda")
-            pp = torch.empty_like(o)
-            outs.append((o, pp))
-            jobs.append(gr.gr_job(g=Gs[gi].handle, op=op, src=src, out=o.data_ptr(),
-                                  pred=pp.data_ptr()))
-        from paper_1701_01170_gb300 import tune
-        b0 = gr.gr_batch_create(jobs)                       # library defaults
-        t0 = _events_ms(lambda: gr.gr_batch_run(b0), args.steps)
-        assert gr.gr_batch_status(b0)[0] == 0
-        gr.gr_batch_destroy(b0)
-        by_handle = {G.handle: G for G in Gs}
-        best_opts, _, chosen = tune.tune_batch_strategy(jobs, by_handle, reps=2)
-        b = gr.gr_batch_create(jobs, gr.batch_opts(**best_opts))
-        ts = _events_ms(lambda: gr.gr_batch_run(b), args.steps)
-        assert gr.gr_batch_status(b)[0] == 0
-
-        def plain():
-            for (gi, op, src), (o, pp) in zip(triples, outs):
-                if op == wl.OP_BFS:
-                    gr.gr_bfs(Gs[gi].handle, src, o, pp)
-                else:
-                    gr.gr_sssp(Gs[gi].handle, src, o, pp)
-        tp = _events_ms(plain, max(1, args.steps // 4), warm=1)
-        ms, mp = statistics.median(ts), statistics.median(tp)
-        emit({"metric": "jobs/s", "value": 512 / ms * 1e3, "unit": "jobs/s", **base,
-              "ms_per_step": ms, "higher_is_better": True,
-              "config": {"workload": "512 BFS/SSSP jobs (50/50) over 64 R-MAT graphs, scale "
-                                     "U{10..18}, ef U{8..32}, weights U[1,64]; one persistent "
-                                     "launch replayed from a CUDA graph; launch shape and "
-                                     "per-level strategy from the batch autotuner",
-                         "batch_opts": best_opts, "tuned": chosen, "info": gr.gr_batch_info(b)},
-              "library_defaults": {"ms": statistics.median(t0),
-                                   "jobs_per_s": 512 / statistics.median(t0) * 1e3},
-              "plain_path": {"ms": mp, "jobs_per_s": 512 / mp * 1e3},
-              "speedup_vs_plain": mp / ms})
-        gr.gr_batch_destroy(b)
+        r = measure_batch(gr, reps=args.steps)
+        emit({"metric": "jobs/s", "value": r["jobs_per_s"], "unit": "jobs/s", **base,
+              "ms_per_step": r["ms"], "higher_is_better": True,
+              "config": {"workload": r["workload"]}, **r})
         return
     if args.workload == "serve":
-        run_serve(args, gr, base)
+        r = measure_serve(gr, [float(x) for x in args.rates.split(",")], args.requests)
+        best = max(r["per_rate"], key=lambda x: x["served"]["queries_per_s"])
+        emit({"metric": "queries/s", "value": best["served"]["queries_per_s"],
+              "unit": "queries/s", **base, "ms_per_step": best["served"]["p50_ms"],
+              "higher_is_better": True, "config": {"workload": r["workload"]}, **r})
         return
 
 
@@ -787,9 +883,100 @@ def host_reached(d, op):
     return a >= 0 if op == "bfs" else a != -1
 
 
-def run_serve(args, gr, base):
-    import numpy as np
+def measure_msbfs(gr, reps):
+    """256-source bit-parallel BFS on R-MAT s20 against 256 plain gr_bfs calls on the same
+    GPU; the depth matrices must be identical."""
     import torch
+
+    import graphgen as gg
+    g = gg.rmat(20, 16, 1)
+    srcs = gg.sources(g, 256, seed=4)
+    G = gr.Graph.from_csr(g)
+    n = g.n
+    D = torch.empty(256 * n, dtype=torch.int32, device="cuda")
+    ts = _events_ms(lambda: gr.gr_bfs_multi(G.handle, srcs, D), reps)
+    P = torch.empty_like(D)
+
+    def plain():
+        for i, s_ in enumerate(srcs):
+            gr.gr_bfs(G.handle, int(s_), P[i * n:(i + 1) * n], None)
+    tp = _events_ms(plain, max(1, reps // 2), warm=1)
+    same = bool(torch.equal(D, P))
+    deg_t = torch.from_numpy(g.degrees().astype(np.int64)).cuda()
+    edges = int(((D.view(256, n) >= 0).to(torch.int64) * deg_t).sum().item())
+    ok = G.sync_status() == gr.GR_OK
+    G.close()
+    ms, mp = statistics.median(ts), statistics.median(tp)
+    return {"workload": "rmat_s20_ef16_seed1: 256-source bit-parallel BFS (sources: 256 "
+                        "random non-isolated vertices, seed 4) vs 256 gr_bfs calls",
+            "ms": ms, "gteps": edges / (ms / 1e3) / 1e9, "queries_per_s": 256 / ms * 1e3,
+            "plain_path": {"ms_256_gr_bfs": mp, "gteps": edges / (mp / 1e3) / 1e9,
+                           "queries_per_s": 256 / mp * 1e3},
+            "speedup_vs_plain": mp / ms, "results_identical": same and ok}
+
+
+def measure_batch(gr, reps):
+    """512 BFS/SSSP jobs over 64 R-MAT graphs in one persistent launch under a CUDA graph
+    (launch shape and per-level strategy from the batch autotuner) against the plain
+    one-query-at-a-time loop; depths, distances and SSSP predecessors must be identical."""
+    import torch
+
+    from graphgen import workloads as wl
+    from paper_1701_01170_gb300 import tune
+    bgs = wl.batch_graphs(64, seed=5)
+    triples = wl.batch_jobs(bgs, 512, seed=5)
+    Gs = [gr.Graph.from_csr(b.csr) for b in bgs]
+    jobs, outs, plain_outs = [], [], []
+    for gi, op, src in triples:
+        o = torch.empty(Gs[gi].n, dtype=torch.int32, device="cuda")
+        pp = torch.empty_like(o)
+        outs.append((o, pp))
+        plain_outs.append((torch.empty_like(o), torch.empty_like(o)))
+        jobs.append(gr.gr_job(g=Gs[gi].handle, op=op, src=src, out=o.data_ptr(),
+                              pred=pp.data_ptr()))
+    b0 = gr.gr_batch_create(jobs)                       # library defaults
+    t0 = _events_ms(lambda: gr.gr_batch_run(b0), reps)
+    ok = gr.gr_batch_status(b0)[0] == 0
+    gr.gr_batch_destroy(b0)
+    by_handle = {G.handle: G for G in Gs}
+    best_opts, _, chosen = tune.tune_batch_strategy(jobs, by_handle, reps=2)
+    b = gr.gr_batch_create(jobs, gr.batch_opts(**best_opts))
+    ts = _events_ms(lambda: gr.gr_batch_run(b), reps)
+    ok = ok and gr.gr_batch_status(b)[0] == 0
+    info = gr.gr_batch_info(b)
+    gr.gr_batch_destroy(b)
+
+    def plain():
+        for (gi, op, src), (o, pp) in zip(triples, plain_outs):
+            if op == wl.OP_BFS:
+                gr.gr_bfs(Gs[gi].handle, src, o, pp)
+            else:
+                gr.gr_sssp(Gs[gi].handle, src, o, pp)
+    tp = _events_ms(plain, max(1, reps // 2), warm=1)
+    same = ok
+    for (gi, op, src), (o, pp), (o2, pp2) in zip(triples, outs, plain_outs):
+        same = same and bool(torch.equal(o, o2))
+        if op == wl.OP_SSSP:                # canonical predecessors (BFS trees may differ)
+            same = same and bool(torch.equal(pp, pp2))
+    same = same and all(G.sync_status() == gr.GR_OK for G in Gs)
+    for G in Gs:
+        G.close()
+    ms, mp = statistics.median(ts), statistics.median(tp)
+    return {"workload": "512 BFS/SSSP jobs (50/50) over 64 R-MAT graphs, scale U{10..18}, ef "
+                        "U{8..32}, weights U[1,64]; one persistent launch replayed from a CUDA "
+                        "graph; launch shape and per-level strategy from the batch autotuner",
+            "ms": ms, "jobs_per_s": 512 / ms * 1e3, "batch_opts": best_opts, "tuned": chosen,
+            "info": info,
+            "library_defaults": {"ms": statistics.median(t0),
+                                 "jobs_per_s": 512 / statistics.median(t0) * 1e3},
+            "plain_path": {"ms": mp, "jobs_per_s": 512 / mp * 1e3},
+            "speedup_vs_plain": mp / ms, "results_identical": same}
+
+
+def measure_serve(gr, rates, requests):
+    """Poisson BFS/SSSP requests over 8 resident graphs through the serving loop, and the same
+    trace one query at a time on the plain path; every result must be identical."""
+    import numpy as np
 
     from graphgen import workloads as wl
     from paper_1701_01170_gb300 import serve
@@ -807,27 +994,29 @@ def run_serve(args, gr, base):
     budget = 96 << 30     # per-lane workspaces; the graphs themselves take about 9 GB
     names = sorted(graphs)
     results = []
-    for rate in [float(x) for x in args.rates.split(",")]:
+    for rate in rates:
         def src_of(name, rng):
             c = cands[name]
             return c[int(rng.integers(0, len(c)))]
-        trace = serve.poisson_trace(names, rate, args.requests, 6, src_of)
+        trace = serve.poisson_trace(names, rate, requests, 6, src_of)
         st = serve.serve_trace(be, trace, lanes, budget, multi_names=multi)
-        trace2 = serve.poisson_trace(names, rate, args.requests, 6, src_of)
+        trace2 = serve.poisson_trace(names, rate, requests, 6, src_of)
         st2 = serve.serve_serial(be, trace2)
         same = all(np.array_equal(a.result, b.result) for a, b in zip(
             sorted(trace, key=lambda r: r.rid), sorted(trace2, key=lambda r: r.rid)))
-        results.append({"rate": rate, "served": st, "serial": st2, "results_identical": same})
+        results.append({"rate": rate, "served": st, "serial": st2, "results_identical": same,
+                        "speedup_vs_serial": (st["queries_per_s"] or 0) /
+                                             max(1e-9, st2["queries_per_s"] or 0)})
     be.close()
-    best = max(results, key=lambda r: r["served"]["queries_per_s"])
-    emit({"metric": "queries/s", "value": best["served"]["queries_per_s"], "unit": "queries/s",
-          **base, "ms_per_step": best["served"]["p50_ms"], "higher_is_better": True,
-          "config": {"workload": "serving: 8 resident graphs (R-MAT s18/20/22/24 ef16, grids "
-                                 "1024^2..8192^2), Poisson BFS/SSSP 50/50, random sources, "
-                                 f"{args.requests} requests per rate, {lanes} lanes, "
-                                 "96 GB workspace budget, R-MAT BFS grouped into "
-                                 "multi-source units", "cta_caps": caps},
-          "per_rate": results})
+    for G in graphs.values():
+        G.close()
+    return {"workload": "serving: 8 resident graphs (R-MAT s18/20/22/24 ef16, grids "
+                        "1024^2..8192^2), Poisson BFS/SSSP 50/50, random sources, "
+                        f"{requests} requests per rate, {lanes} lanes, 96 GB workspace budget, "
+                        "R-MAT BFS grouped into multi-source units; serial = the same trace "
+                        "one query at a time on the plain path",
+            "cta_caps": caps, "per_rate": results,
+            "results_identical": all(r["results_identical"] for r in results)}
 
 
 def main():

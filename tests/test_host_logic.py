@@ -66,7 +66,32 @@ def test_profiled_traffic_reads_matching_summaries(tmp_path, monkeypatch):
         "- kernel_source_digest: `0000000000000000`\n- traffic_bytes_per_launch: 99\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     got = bench.profiled_traffic()
-    assert got == {"bfs": 1234, "sssp": None}     # a stale summary gives no traffic
+    # a stale summary gives no traffic, and so does a missing one
+    assert got == {"bfs": 1234, "sssp": None, "push_bfs": None}
+
+
+def test_roofline_bytes_follow_the_per_unit_formulas():
+    import bench
+    n, m_r, n_r = 1000, 50_000, 800
+    # push BFS: 4 B per column of a reached row, 24 B per reached vertex, 8 B per vertex
+    assert bench.algorithmic_bytes("push_bfs", n, m_r=m_r, n_r=n_r) == 4 * m_r + 24 * n_r + 8 * n
+    # SSSP lower bound: every edge of a reached vertex relaxed once (column + weight),
+    # 28 B per vertex; repeated relaxations are not counted
+    assert bench.algorithmic_bytes("sssp", n, m_r=m_r, n_r=n_r) == 8 * m_r + 28 * n
+    st = {"edges": 7000, "vertices": 300, "updates": 250}
+    assert bench.algorithmic_bytes("bfs", n, st=st) == 4 * 7000 + 12 * 300 + 12 * 250 + 8 * n
+    e = bench.roofline_entry("k", "l", 2e9, 1.0, 4000.0, "measured", None)
+    assert abs(e["achieved"] - 2000.0) < 1e-9 and abs(e["frac"] - 0.5) < 1e-12
+
+
+def test_timed_sources_start_at_the_hub_and_warmup_uses_others():
+    import bench
+    srcs = list(range(100, 165))          # 65 entries, entry 0 plays the hub
+    assert bench.timed_sources(srcs, 0, 20) == srcs[:20]
+    assert bench.timed_sources(srcs, 1, 3) == srcs[7:10]
+    assert bench.timed_sources(srcs, 0, 70)[65:] == srcs[:5]      # wraps around the list
+    w = bench.warmup_sources(srcs, 5)
+    assert w == srcs[-5:][::-1] and srcs[0] not in w
 
 
 def test_operator_bytes_and_peak_fallback(tmp_path, monkeypatch):
