@@ -275,6 +275,15 @@ typedef struct gr_bfs_opts {
                             latency-bound levels) loses little on a quarter
                             of the SMs, and several such queries on separate
                             streams then run side by side                   */
+  int64_t bulk_edges;    /* push levels whose frontier has at least this many
+                            edges run in bulk: the expansion only marks
+                            unvisited targets in the next-frontier bitmap
+                            (reductions without return values), then one
+                            pass over that bitmap writes the depths and
+                            builds the next frontier; smaller push levels
+                            claim each target with an atomic as they go.
+                            0 = default (n / 8, at least 65536), < 0 =
+                            never.  Results do not depend on it             */
 } gr_bfs_opts;
 
 /* Fill *o with the library defaults. */

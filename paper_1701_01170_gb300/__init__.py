@@ -42,7 +42,8 @@ GR_DIR_AUTO, GR_DIR_PUSH, GR_DIR_PULL = 0, 1, 2
 class gr_bfs_opts(ctypes.Structure):
     _fields_ = [("direction", c_i32), ("do_a", c_f32), ("do_b", c_f32), ("big_degree", c_i32),
                 ("blocks_per_sm", c_i32), ("spin_limit", c_u32), ("ws", c_vp),
-                ("level_stats", c_vp), ("max_levels", c_i32), ("max_blocks", c_i32)]
+                ("level_stats", c_vp), ("max_levels", c_i32), ("max_blocks", c_i32),
+                ("bulk_edges", c_i64)]
 
 
 class gr_sssp_opts(ctypes.Structure):

@@ -135,6 +135,20 @@ __global__ void gr_validate_edges(int32_t n, const int32_t* __restrict__ R,
   }
 }
 
+// Bit v of word w is set when vertex v = 32 w + bit has no edges.
+__global__ void gr_zero_degree_bitmap(int32_t n, const int32_t* __restrict__ R, uint32_t* bm,
+                                      int64_t nwords) {
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t x = 0u;
+    for (int b = 0; b < 32; ++b) {
+      const int64_t v = w * 32 + b;
+      if (v < n && R[v + 1] == R[v]) x |= 1u << b;
+    }
+    bm[w] = x;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // workspaces
 
@@ -367,6 +381,7 @@ extern "C" gr_status gr_graph_create_csr(int32_t n, int64_t m, const int32_t* ro
   auto fail = [&](gr_status st) {
     for (void* p : g->owned)
       if (p) cudaFree(p);
+    if (g->zero_deg) cudaFree(g->zero_deg);
     delete g;
     return st;
   };
@@ -428,6 +443,18 @@ extern "C" gr_status gr_graph_create_csr(int32_t n, int64_t m, const int32_t* ro
   g->max_degree = h_out.max_degree;
   g->nonisolated = h_out.nonisolated;
   g->weight_sum = h_out.weight_sum;
+  if ((flags & GR_SYMMETRIC) && g->nonisolated < n) {
+    const int64_t nw = (int64_t)bitmap_words(n);
+    if (cudaMalloc((void**)&g->zero_deg, nw * sizeof(uint32_t)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return fail(GR_ERR_OOM);
+    }
+    gr_zero_degree_bitmap<<<g->num_sms * 4, 256, 0, s>>>(n, g->R, g->zero_deg, nw);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return fail(GR_ERR_CUDA);
+    }
+  }
   // an edgeless graph needs no weight array to be a valid SSSP input
   const bool weighted = weights != nullptr || m == 0;
   gr_status st = ws_create(g, weighted ? (GR_OP_BFS | GR_OP_SSSP) : GR_OP_BFS, &g->ws_default);
@@ -441,6 +468,7 @@ extern "C" gr_status gr_graph_destroy(gr_graph* g) {
   cudaDeviceSynchronize();
   ws_free(g->ws_default);
   gr_ms_free(g->ms);
+  if (g->zero_deg) cudaFree(g->zero_deg);
   for (void* p : g->owned)
     if (p) cudaFree(p);
   delete g;

@@ -43,6 +43,21 @@ __global__ void __launch_bounds__(NT, GR_BFS_MIN_BLOCKS) bfs_persistent(BfsArgs 
   gr_bfs_body(a, sc, ar);
 }
 
+#ifndef GR_BFS_CARVEOUT
+#define GR_BFS_CARVEOUT -1  // preferred shared-memory share of L1 in percent; -1: driver default
+#endif
+// Sets the kernel's preferred L1 / shared-memory split once per process.
+void bfs_carveout_once() {
+#if GR_BFS_CARVEOUT >= 0
+  static std::once_flag once;
+  std::call_once(once, [] {
+    (void)cudaFuncSetAttribute((const void*)bfs_persistent,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, GR_BFS_CARVEOUT);
+    (void)cudaGetLastError();
+  });
+#endif
+}
+
 }  // namespace
 
 extern "C" void gr_bfs_opts_default(gr_bfs_opts* o) {
@@ -57,6 +72,7 @@ extern "C" void gr_bfs_opts_default(gr_bfs_opts* o) {
   o->level_stats = nullptr;
   o->max_levels = 0;
   o->max_blocks = 0;
+  o->bulk_edges = 0;
 }
 
 extern "C" gr_status gr_bfs(const gr_graph* g, int32_t src, int32_t* depth, int32_t* pred,
@@ -105,7 +121,11 @@ extern "C" gr_status gr_bfs(const gr_graph* g, int32_t src, int32_t* depth, int3
   a.spin = o.spin_limit ? o.spin_limit : GR_DEFAULT_SPIN_LIMIT;
   a.level_stats = o.level_stats;
   a.max_levels = o.max_levels;
+  a.bulk_edges = o.bulk_edges < 0 ? 0 : (o.bulk_edges > 0 ? o.bulk_edges
+                                                          : gr_default_bulk_edges(g->n));
+  a.preset = symmetric ? g->zero_deg : nullptr;
 
+  bfs_carveout_once();
   int blocks = gr_launch_blocks((const void*)bfs_persistent, NT, 0, g->num_sms,
                                 o.blocks_per_sm);
   if (blocks <= 0) return GR_ERR_CUDA;
@@ -249,6 +269,7 @@ extern "C" gr_status gr_bfs_static(int32_t n, int64_t m, const int32_t* row_offs
   a.spin = GR_DEFAULT_SPIN_LIMIT;
   a.level_stats = nullptr;
   a.max_levels = 0;
+  a.bulk_edges = gr_default_bulk_edges(n);
 
   // the control block and the status word must start at zero; the rest of
   // the scratch is initialised by the kernel itself

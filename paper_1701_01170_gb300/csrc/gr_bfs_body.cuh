@@ -11,6 +11,22 @@
 #ifndef GR_VISIT_STRIPS
 #define GR_VISIT_STRIPS 4  // 32-edge strips a warp expands per round
 #endif
+#ifndef GR_BULK_PUSH_STRIPS
+#define GR_BULK_PUSH_STRIPS 4  // strips per round in the mark pass of a bulk push level
+#endif
+#ifndef GR_COLLECT_ROUNDS
+#define GR_COLLECT_ROUNDS 4    // new vertices per lane in flight in the collect pass
+#endif
+// Push levels whose frontier has at least max(n / GR_BULK_PUSH_DIVISOR,
+// GR_BULK_PUSH_MIN) edges run in bulk (see gr_bfs_body).  Below that (a
+// single hub row of R-MAT s22: 163 K edges) claiming as the edges arrive is
+// faster than a pass over the whole bitmap (23 us against 57 us).
+#define GR_BULK_PUSH_DIVISOR 8
+#define GR_BULK_PUSH_MIN (1 << 16)
+__host__ __device__ inline int64_t gr_default_bulk_edges(int64_t n) {
+  const int64_t e = n / GR_BULK_PUSH_DIVISOR;
+  return e > GR_BULK_PUSH_MIN ? e : GR_BULK_PUSH_MIN;
+}
 
 struct BfsArgs {
   int32_t n;
@@ -38,6 +54,10 @@ struct BfsArgs {
   unsigned spin;
   int32_t* level_stats;
   int32_t max_levels;
+  int64_t bulk_edges;  // push levels with a frontier of at least this many edges run in bulk
+                       // (0: never); needs the frontier bitmaps front[]
+  const uint32_t* preset;  // n-bit bitmap of vertices that start as visited (isolated vertices
+                           // of a symmetric graph, which no edge reaches) or NULL
 };
 
 // The whole BFS (init + level loop) for one query, executed by the threads
@@ -63,10 +83,14 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
   }
   const int32_t sw = a.src >> 5;
   const uint32_t sbit = 1u << (a.src & 31);
+  // frontier bitmaps: the next frontier of pull levels and bulk push levels
+  const bool bitmaps = a.use_do || a.bulk_edges > 0;
   for (int64_t w = gtid; w < a.nwords; w += gthreads) {
-    uint32_t x = w == sw ? sbit : 0u;
-    a.visited[w] = x;
-    if (a.use_do) {
+    const uint32_t x = w == sw ? sbit : 0u;
+    // isolated vertices start as visited, so that pull levels do not probe
+    // them (on R-MAT s22 they are 43 % of the vertices); their depth stays -1
+    a.visited[w] = a.preset ? (__ldg(a.preset + w) | x) : x;
+    if (bitmaps) {
       a.front[0][w] = x;
       a.front[1][w] = 0u;
       a.front[2][w] = 0u;
@@ -162,7 +186,7 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
       ctl->qbuilt[s2] = 0;
       ctl->ulen[s2] = 0;
     }
-    if (a.use_do)
+    if (bitmaps)
       for (int64_t w = gtid; w < a.nwords; w += gthreads) a.front[s2][w] = 0u;
 
     if (!pull && prev_pull) {
@@ -223,7 +247,100 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
     const int next_depth = L + 1;
     const bool list_pull = pull && list_ready;
 
-    if (!pull) {
+    const bool bulk_push = !pull && a.bulk_edges > 0 && mf >= (unsigned long long)a.bulk_edges;
+    if (bulk_push) {
+      // ---- bulk push: advance + visit + cull as two passes ----------------
+      // Mark: for every edge (u, v), v's word of the visited bitmap (vertices
+      // of earlier levels; read-only during this pass, so it may be served
+      // from L1) is loaded with the column; only a target it does not hold
+      // reads its next-frontier word from L2, and if that bit is clear too,
+      // sets it with a reduction that returns nothing and records u as v's
+      // parent (several frontier vertices may store; each is a valid parent
+      // one level up).  No per-edge atomic returns a value and no discovery
+      // is classified inside the edge loop.
+      const int32_t* q = a.q[L & 1];
+      const int2* ch = a.ch[L & 1];
+      auto pre = [&](bool active, int, int32_t v) -> uint32_t {
+        return active ? a.visited[v >> 5] : 0u;
+      };
+      auto mark = [&](bool active, int32_t u, uint32_t, int, int32_t v, uint32_t vis) {
+        if (!active) return;
+        ++cnt.edges;
+        const uint32_t b1 = 1u << (v & 31);
+        if (!(vis & b1) && !(__ldcg(fnext + (v >> 5)) & b1)) {
+          gr_red_or_u32(fnext + (v >> 5), b1);
+          if (a.pred) a.pred[v] = u;
+        }
+      };
+      auto no_payload = [](int32_t) -> uint32_t { return 0u; };
+      gr_chunks_loop<GR_BULK_PUSH_STRIPS>(ch, nch, swarp, (int)nwarps, lane, a.R, a.C, cnt,
+                                          no_payload, pre, mark);
+      if (a.qm[0])
+        gr_rows_loop<GR_BULK_PUSH_STRIPS>(a.qm[L & 1], nqm, GR_MEDIUM_BATCH, &ctl->workm[s0],
+                                          swarp, (int)nwarps, lane, a.R, a.C, cnt, no_payload,
+                                          pre, mark);
+      gr_rows_loop<GR_BULK_PUSH_STRIPS>(q, nq, 32, &ctl->work[s0], swarp, (int)nwarps, lane, a.R,
+                                        a.C, cnt, no_payload, pre, mark);
+      if (!sc.sync()) return;
+      // Collect: one pass over the next-frontier bitmap.  Its set bits are
+      // exactly this level's discoveries (a bit is only set for a vertex that
+      // was unvisited when the level began).  Lane l of warp s takes the
+      // words s + (l + 32 k) * nwarps, so the words of one warp lie far apart
+      // and a dense run of discoveries (a hub's neighbourhood has clustered
+      // ids) spreads over every CTA and its staging buffers.  The lane merges
+      // its word into the visited bitmap; the set bits of the warp's 32 words
+      // are then dealt out evenly over the lanes (a prefix count of the words'
+      // bits, then each lane finds its bit), GR_COLLECT_ROUNDS vertices per
+      // lane with their row loads in flight together.  Each new vertex gets
+      // its depth and joins a row class of the next level.
+      for (int64_t wk = swarp; wk < a.nwords; wk += 32 * nwarps) {
+        const int64_t w = wk + (int64_t)lane * nwarps;
+        uint32_t word = w < a.nwords ? __ldcg(fnext + w) : 0u;
+        if (word) a.visited[w] = __ldcg(a.visited + w) | word;
+        int total;
+        const int excl = gr_warp_excl_scan(__popc(word), lane, &total);
+        for (int base = 0; base < total; base += 32 * GR_COLLECT_ROUNDS) {
+          int32_t v[GR_COLLECT_ROUNDS];
+          bool mine[GR_COLLECT_ROUNDS];
+#pragma unroll
+          for (int k = 0; k < GR_COLLECT_ROUNDS; ++k) {
+            const int p = base + k * 32 + lane;
+            int lo = 0;  // the lane whose word holds the p-th bit of the batch
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+              const int cand = lo + step;
+              if (__shfl_sync(GR_FULL_MASK, excl, cand) <= p) lo = cand;
+            }
+            const uint32_t ow = __shfl_sync(GR_FULL_MASK, word, lo);
+            const int r = p - __shfl_sync(GR_FULL_MASK, excl, lo);
+            mine[k] = p < total;
+            v[k] = mine[k] ? (int32_t)((wk + (int64_t)lo * nwarps) * 32 + gr_nth_set_bit(ow, r)) : 0;
+          }
+          int vb[GR_COLLECT_ROUNDS], vd[GR_COLLECT_ROUNDS];
+#pragma unroll
+          for (int k = 0; k < GR_COLLECT_ROUNDS; ++k) {
+            vb[k] = mine[k] ? __ldg(a.R + v[k]) : 0;
+            vd[k] = mine[k] ? __ldg(a.R + v[k] + 1) : 0;
+          }
+#pragma unroll
+          for (int k = 0; k < GR_COLLECT_ROUNDS; ++k) {
+            vd[k] -= vb[k];
+            if (mine[k]) {
+              ++cnt.updates;
+              a.depth[v[k]] = next_depth;
+              my_mf += (unsigned long long)vd[k];
+            }
+            const bool big = mine[k] && vd[k] >= a.big;
+            const bool mid = mine[k] && !big && qmn && vd[k] >= GR_MEDIUM_DEGREE;
+            stage.append(qn, &ctl->qlen[s1], a.n, mine[k] && !big && !mid, v[k], lane);
+            mstage.append(qmn, &ctl->qmlen[s1], a.n, mid, v[k], lane);
+            if (big)
+              bstage.add(chn, a.chunk_cap, &ctl->nchunk[s1], &ctl->nbig[s1], v[k], vb[k], vd[k],
+                         a.status);
+          }
+        }
+      }
+    } else if (!pull) {
       // ---- push: advance + visit + cull fused ----------------------------
       const int32_t* q = a.q[L & 1];
       const int2* ch = a.ch[L & 1];

@@ -128,6 +128,8 @@ struct gr_graph {
   int num_sms;
   gr_workspace* ws_default;
   GrMsState* ms;                   // allocated by the first gr_bfs_multi call
+  uint32_t* zero_deg;              // symmetric graphs with isolated vertices: n-bit bitmap of
+                                   // the vertices without edges (no BFS can reach them)
 };
 
 struct gr_workspace {
@@ -744,6 +746,22 @@ struct GrArena {
   int buf1[GR_STAGE_CAP];  // BFS unvisited list / SSSP far pile
   int bv[GR_BIG_STAGE_CAP], bb[GR_BIG_STAGE_CAP], bd[GR_BIG_STAGE_CAP], bo[GR_BIG_STAGE_CAP];
 };
+
+// Position of the r-th (0-based) set bit of w; w must have more than r set
+// bits.  Five halving steps on population counts.
+__device__ __forceinline__ int gr_nth_set_bit(uint32_t w, int r) {
+  int pos = 0;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const int c = __popc(w & ((1u << s) - 1u));
+    if (c <= r) {
+      r -= c;
+      w >>= s;
+      pos += s;
+    }
+  }
+  return pos;
+}
 
 // Warp-wide minimum of an unsigned.
 __device__ __forceinline__ unsigned gr_warp_min_u32(unsigned x) {

@@ -65,7 +65,7 @@ def test_option_struct_layouts_match_header(lib_path):
     assert o.direction == gr.GR_DIR_AUTO and o.big_degree > 0 and o.spin_limit > 0
     s = gr.sssp_opts()
     assert s.delta == 0 and s.big_degree > 0
-    assert ctypes.sizeof(gr.gr_bfs_opts) == 48
+    assert ctypes.sizeof(gr.gr_bfs_opts) == 56
     assert ctypes.sizeof(gr.gr_sssp_opts) == 48
     assert ctypes.sizeof(gr.gr_bfs_state) == 24
     assert ctypes.sizeof(gr.gr_sssp_state) == 16

@@ -52,10 +52,13 @@ def test_config_s16_from_vertex0(gr, s16):
 
 @pytest.mark.parametrize("direction", [0, 1, 2])
 @pytest.mark.parametrize("big", [32, 100, 1024, 1 << 30])
-def test_directions_and_split_thresholds_agree(gr, s16, direction, big):
+@pytest.mark.parametrize("bulk", [0, 1, -1])
+def test_directions_and_split_thresholds_agree(gr, s16, direction, big, bulk):
+    # bulk: push levels of at least bulk_edges frontier edges mark a bitmap and list it
+    # afterwards (0 = default threshold, 1 = every push level, -1 = none)
     g, G = s16
     for src in (0, 12345, int(gg.sources(g, 1, seed=9)[0])):
-        d, p = run_bfs(gr, G, src, direction=direction, big_degree=big)
+        d, p = run_bfs(gr, G, src, direction=direction, big_degree=big, bulk_edges=bulk)
         check(g, src, d, p)
 
 
@@ -97,8 +100,10 @@ def test_small_and_degenerate_graphs(gr):
         G = gr.Graph.from_csr(g)
         for direction in (0, 1, 2):
             for big in (32, 1024):
-                d, p = run_bfs(gr, G, src, direction=direction, big_degree=big)
-                check(g, src, d, p)
+                for bulk in (1, -1):
+                    d, p = run_bfs(gr, G, src, direction=direction, big_degree=big,
+                                   bulk_edges=bulk)
+                    check(g, src, d, p)
         G.close()
 
 
@@ -156,8 +161,9 @@ def test_directed_graph_push_only(gr):
     pairs = np.unique(np.stack([s[keep], t[keep]], 1), axis=0)
     g = gg.directed(n, pairs[:, 0], pairs[:, 1])
     G = gr.Graph.from_csr(g, symmetric=False)
-    d, p = run_bfs(gr, G, 0)
-    check(g, 0, d, p)
+    for bulk in (0, 1, -1):        # bulk push levels work without a transpose too
+        d, p = run_bfs(gr, G, 0, bulk_edges=bulk)
+        check(g, 0, d, p)
     with pytest.raises(gr.GrError):
         run_bfs(gr, G, 0, direction=gr.GR_DIR_PULL)
 
@@ -274,8 +280,9 @@ def test_config_s22_full_size(gr):
     for src in [hub] + list(gg.sources(g, 2, seed=2)):
         d, p = run_bfs(gr, G, int(src))
         check(g, int(src), d, p)
-    d2, p2 = run_bfs(gr, G, hub, direction=gr.GR_DIR_PUSH)
-    check(g, hub, d2, p2)
+    for bulk in (0, -1):           # push only: bulk levels (default) and atomic claims
+        d2, p2 = run_bfs(gr, G, hub, direction=gr.GR_DIR_PUSH, bulk_edges=bulk)
+        check(g, hub, d2, p2)
     G.close()
 
 
