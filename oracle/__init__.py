@@ -15,6 +15,11 @@ share no code.  Functions cite the passage of the paper they follow:
 * ``filter_unique``, ``filter_unvisited``, ``filter_near_far`` — Sec. 4.2,
                        Alg. 2 GenerateUnvisitedFrontier, Sec. 5.1.5 near/far.
 * ``bfs_certificate``, ``sssp_certificate`` — textbook optimality conditions.
+* ``bc_source``, ``bc`` — Sec. 6.3, Brandes' path counts (int64) and dependencies.
+* ``cc``             — Sec. 6.4, component labels (smallest vertex id of the component).
+* ``segmented_intersect`` — Sec. 4.3, neighbour-list intersections of item pairs.
+* ``triangles``      — Sec. 6.6, triangles by their definition (each once, u < v < w).
+* ``multisplit``     — Sec. 5.1.5's near/far split generalised to K buckets.
 
 Parity status: every function is pinned by ``tests/test_oracle_pins.py``
 (closed forms, scipy's independent csgraph routines, brute force, hand-worked
@@ -72,6 +77,12 @@ def _load():
                 "orc_bfs_certificate": ([i32, vp, vp, i32, vp, vp], i32),
                 "orc_sssp_certificate": ([i32, vp, vp, vp, i32, vp, vp], i32),
                 "orc_bfs_multi": ([i32, vp, vp, vp, i32, vp], i32),
+                "orc_bc_source": ([i32, vp, vp, i32, vp, vp, vp], i32),
+                "orc_bc": ([i32, vp, vp, vp, i32, vp], i32),
+                "orc_cc": ([i32, vp, vp, vp], i64),
+                "orc_segmented_intersect": ([vp, vp, vp, vp, i64, vp, vp, i64], i64),
+                "orc_triangles": ([i32, vp, vp, vp], i64),
+                "orc_multisplit": ([i32, vp, i64, vp, u32, u32, i32, vp, vp], i64),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -248,3 +259,78 @@ def bfs_multi(R, C, srcs):
     if _load().orc_bfs_multi(n, _p(R), _p(C), _p(S), len(S), _p(depth)) < 0:
         raise ValueError("bad multi-source BFS arguments")
     return depth
+
+
+def bc_source(R, C, src: int):
+    """Brandes' single-source pass (Sec. 6.3).  Returns (depth int32, sigma int64,
+    delta float64, overflow); sigma counts shortest paths, delta is the dependency."""
+    R, C = _i32(R), _i32(C)
+    n = len(R) - 1
+    depth = np.empty(n, np.int32)
+    sigma = np.empty(n, np.int64)
+    delta = np.empty(n, np.float64)
+    rc = _load().orc_bc_source(n, _p(R), _p(C), src, _p(depth), _p(sigma), _p(delta))
+    if rc < 0:
+        raise ValueError("bad BC arguments")
+    return depth, sigma, delta, bool(rc)
+
+
+def bc(R, C, srcs):
+    """Betweenness centrality over the given sources (ordered pairs): float64 array."""
+    R, C, S = _i32(R), _i32(C), _i32(srcs)
+    n = len(R) - 1
+    out = np.empty(n, np.float64)
+    rc = _load().orc_bc(n, _p(R), _p(C), _p(S), len(S), _p(out))
+    if rc < 0:
+        raise ValueError("bad BC arguments")
+    if rc > 0:
+        raise OverflowError("a shortest-path count exceeds INT64_MAX")
+    return out
+
+
+def cc(R, C):
+    """Component labels (smallest vertex id of each component) and the component count."""
+    R, C = _i32(R), _i32(C)
+    n = len(R) - 1
+    label = np.empty(max(n, 1), np.int32)
+    k = _load().orc_cc(n, _p(R), _p(C), _p(label))
+    if k < 0:
+        raise MemoryError("oracle CC")
+    return label[:n].copy(), int(k)
+
+
+def segmented_intersect(R, C, a, b, items: bool = True):
+    """Per-pair intersection sizes of N(a[i]) and N(b[i]) and, with items, the
+    intersections concatenated in pair order.  Returns (counts int64, items or None, total)."""
+    R, C, A, B = _i32(R), _i32(C), _i32(a), _i32(b)
+    counts = np.empty(max(len(A), 1), np.int64)
+    lib = _load()
+    total = lib.orc_segmented_intersect(_p(R), _p(C), _p(A), _p(B), len(A), _p(counts), None, 0)
+    out = None
+    if items:
+        out = np.empty(max(total, 1), np.int32)
+        lib.orc_segmented_intersect(_p(R), _p(C), _p(A), _p(B), len(A), _p(counts), _p(out),
+                                    total)
+        out = out[:total].copy()
+    return counts[:len(A)].copy(), out, int(total)
+
+
+def triangles(R, C):
+    """(total triangles, per-vertex triangle counts int64) of an undirected graph."""
+    R, C = _i32(R), _i32(C)
+    n = len(R) - 1
+    per = np.empty(max(n, 1), np.int64)
+    t = _load().orc_triangles(n, _p(R), _p(C), _p(per))
+    if t < 0:
+        raise MemoryError("oracle triangles")
+    return int(t), per[:n].copy()
+
+
+def multisplit(n: int, items, dist, base: int, delta: int, K: int):
+    """Stable K-way split by bucket min(K-1, (dist - base) // delta) (0 below base).
+    Returns (items by bucket, bucket lengths int64[K])."""
+    a, d = _i32(items), _u32(dist)
+    out = np.empty(max(len(a), 1), np.int32)
+    bl = np.empty(K, np.int64)
+    w = _load().orc_multisplit(n, _p(a), len(a), _p(d), base, delta, K, _p(out), _p(bl))
+    return out[:w].copy(), bl

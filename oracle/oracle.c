@@ -468,3 +468,190 @@ int32_t orc_bfs_multi(int32_t n, const int32_t* R, const int32_t* C, const int32
     if (orc_bfs(n, R, C, srcs[i], depth + (int64_t)i * n, NULL) < 0) return -1;
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Betweenness centrality, one source (Sec. 6.3: Brandes' formulation, a     */
+/* forward BFS pass that accumulates path counts and a backward pass over    */
+/* the BFS levels that accumulates dependencies).                           */
+/*   depth: BFS depth from src (-1 unreachable);                             */
+/*   sigma[v]: number of shortest src -> v paths (sigma[src] = 1, 0 if       */
+/*     unreachable), the sum of sigma[u] over edges (u, v) with              */
+/*     depth[v] = depth[u] + 1;                                              */
+/*   delta[u]: dependency of src on u, the sum over edges (u, v) with        */
+/*     depth[v] = depth[u] + 1 of sigma[u] / sigma[v] * (1 + delta[v]),      */
+/*     taken in reverse BFS order so that every delta[v] on the right is     */
+/*     final (0 for unreachable vertices; delta[src] is computed the same    */
+/*     way).                                                                */
+/* Returns 0, 1 if some path count exceeds INT64_MAX (the counts are then    */
+/* meaningless), or -1 on bad arguments / allocation failure.               */
+/* ------------------------------------------------------------------------ */
+int32_t orc_bc_source(int32_t n, const int32_t* R, const int32_t* C, int32_t src,
+                      int32_t* depth, int64_t* sigma, double* delta) {
+  if (n <= 0 || src < 0 || src >= n) return -1;
+  int32_t* order = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+  if (!order) return -1;
+  for (int32_t v = 0; v < n; ++v) { depth[v] = -1; sigma[v] = 0; delta[v] = 0.0; }
+  int32_t ovf = 0;
+  int64_t head = 0, tail = 0;
+  depth[src] = 0;
+  sigma[src] = 1;
+  order[tail++] = src;
+  while (head < tail) {                      /* forward pass: FIFO BFS order */
+    int32_t u = order[head++];
+    for (int64_t e = R[u]; e < R[u + 1]; ++e) {
+      int32_t v = C[e];
+      if (depth[v] == -1) { depth[v] = depth[u] + 1; order[tail++] = v; }
+      if (depth[v] == depth[u] + 1 && __builtin_add_overflow(sigma[v], sigma[u], &sigma[v]))
+        ovf = 1;
+    }
+  }
+  for (int64_t i = tail - 1; i >= 0; --i) {  /* backward pass: reverse BFS order */
+    int32_t u = order[i];
+    double d = 0.0;
+    for (int64_t e = R[u]; e < R[u + 1]; ++e) {
+      int32_t v = C[e];
+      if (depth[v] == depth[u] + 1)
+        d += ((double)sigma[u] / (double)sigma[v]) * (1.0 + delta[v]);
+    }
+    delta[u] = d;
+  }
+  free(order);
+  return ovf;
+}
+
+/* BC over a set of sources: bc[v] = sum over the k sources s != v of the     */
+/* dependency of s on v (ordered source/target pairs, Brandes' definition).  */
+/* Returns 0, 1 on path-count overflow, -1 on bad arguments.                 */
+int32_t orc_bc(int32_t n, const int32_t* R, const int32_t* C, const int32_t* srcs, int32_t k,
+               double* bc) {
+  if (n <= 0) return -1;
+  int32_t* depth = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+  int64_t* sigma = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+  double* delta = (double*)malloc((size_t)n * sizeof(double));
+  if (!depth || !sigma || !delta) { free(depth); free(sigma); free(delta); return -1; }
+  for (int32_t v = 0; v < n; ++v) bc[v] = 0.0;
+  int32_t rc = 0;
+  for (int32_t i = 0; i < k && rc >= 0; ++i) {
+    int32_t r = orc_bc_source(n, R, C, srcs[i], depth, sigma, delta);
+    if (r < 0) { rc = -1; break; }
+    if (r > 0) rc = 1;
+    for (int32_t v = 0; v < n; ++v)
+      if (v != srcs[i]) bc[v] += delta[v];
+  }
+  free(depth); free(sigma); free(delta);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Connected components (Sec. 6.4) of an undirected (symmetric) graph:       */
+/* label[v] = the smallest vertex id of v's component.  Vertices are taken   */
+/* in increasing id order; each unlabelled one starts a BFS that labels its  */
+/* whole component with its own id, which is therefore the component's      */
+/* smallest.  Returns the number of components, or -1 on allocation failure. */
+/* ------------------------------------------------------------------------ */
+int64_t orc_cc(int32_t n, const int32_t* R, const int32_t* C, int32_t* label) {
+  int32_t* queue = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+  if (!queue) return -1;
+  for (int32_t v = 0; v < n; ++v) label[v] = -1;
+  int64_t comps = 0;
+  for (int32_t s = 0; s < n; ++s) {
+    if (label[s] != -1) continue;
+    ++comps;
+    int64_t head = 0, tail = 0;
+    label[s] = s;
+    queue[tail++] = s;
+    while (head < tail) {
+      int32_t u = queue[head++];
+      for (int64_t e = R[u]; e < R[u + 1]; ++e)
+        if (label[C[e]] == -1) { label[C[e]] = s; queue[tail++] = C[e]; }
+    }
+  }
+  free(queue);
+  return comps;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Segmented intersection (Sec. 4.3): for every pair i, the ids present in   */
+/* both neighbour lists N(a[i]) and N(b[i]) (rows sorted ascending without   */
+/* duplicates), by a two-pointer merge.  counts[i] = size of pair i's        */
+/* intersection; if out != NULL the intersections are written in pair order, */
+/* each ascending, up to out_cap items.  Returns the total count.            */
+/* ------------------------------------------------------------------------ */
+int64_t orc_segmented_intersect(const int32_t* R, const int32_t* C, const int32_t* a,
+                                const int32_t* b, int64_t len, int64_t* counts, int32_t* out,
+                                int64_t out_cap) {
+  int64_t total = 0;
+  for (int64_t i = 0; i < len; ++i) {
+    int64_t x = R[a[i]], xe = R[a[i] + 1], y = R[b[i]], ye = R[b[i] + 1], c = 0;
+    while (x < xe && y < ye) {
+      if (C[x] < C[y]) ++x;
+      else if (C[y] < C[x]) ++y;
+      else {
+        if (out && total + c < out_cap) out[total + c] = C[x];
+        ++c; ++x; ++y;
+      }
+    }
+    counts[i] = c;
+    total += c;
+  }
+  return total;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Triangle counting (Sec. 6.6), by the definition: every triangle           */
+/* {u, v, w} of an undirected graph (u < v < w, all three edges present) is  */
+/* counted once; per_vertex[x] = the number of triangles that contain x      */
+/* (NULL allowed).  Neighbour lists of u are marked in a flag array; for     */
+/* each v > u adjacent to u and each w > v adjacent to v, a marked w closes  */
+/* a triangle.  Returns the number of triangles (-1 on allocation failure).  */
+/* ------------------------------------------------------------------------ */
+int64_t orc_triangles(int32_t n, const int32_t* R, const int32_t* C, int64_t* per_vertex) {
+  uint8_t* mark = (uint8_t*)calloc((size_t)(n > 0 ? n : 1), 1);
+  if (!mark) return -1;
+  if (per_vertex) for (int32_t v = 0; v < n; ++v) per_vertex[v] = 0;
+  int64_t total = 0;
+  for (int32_t u = 0; u < n; ++u) {
+    for (int64_t e = R[u]; e < R[u + 1]; ++e) mark[C[e]] = 1;
+    for (int64_t e = R[u]; e < R[u + 1]; ++e) {
+      int32_t v = C[e];
+      if (v <= u) continue;
+      for (int64_t f = R[v]; f < R[v + 1]; ++f) {
+        int32_t w = C[f];
+        if (w <= v || !mark[w]) continue;
+        ++total;
+        if (per_vertex) { ++per_vertex[u]; ++per_vertex[v]; ++per_vertex[w]; }
+      }
+    }
+    for (int64_t e = R[u]; e < R[u + 1]; ++e) mark[C[e]] = 0;
+  }
+  free(mark);
+  return total;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Multisplit (the multi-level priority queue of Sec. 5.1.5 generalised to   */
+/* K buckets): item v in [0, n) goes to bucket                               */
+/*   b(v) = 0 if dist[v] < base, else min(K - 1, (dist[v] - base) / delta);  */
+/* out = the items of bucket 0 in input order, then bucket 1, ..., and       */
+/* bucket_len[j] = the number of items in bucket j.  Items outside [0, n)   */
+/* are dropped.  Returns the number of items written.                        */
+/* ------------------------------------------------------------------------ */
+int64_t orc_multisplit(int32_t n, const int32_t* in, int64_t len, const uint32_t* dist,
+                       uint32_t base, uint32_t delta, int32_t K, int32_t* out,
+                       int64_t* bucket_len) {
+  int64_t w = 0;
+  for (int32_t j = 0; j < K; ++j) {
+    bucket_len[j] = 0;
+    for (int64_t i = 0; i < len; ++i) {
+      int32_t v = in[i];
+      if (v < 0 || v >= n) continue;
+      uint32_t d = dist[v];
+      uint64_t b = d < base ? 0 : (uint64_t)(d - base) / delta;
+      if (b > (uint64_t)(K - 1)) b = (uint64_t)(K - 1);
+      if ((int32_t)b != j) continue;
+      out[w++] = v;
+      ++bucket_len[j];
+    }
+  }
+  return w;
+}
