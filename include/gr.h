@@ -421,6 +421,42 @@ gr_status gr_batch_info(const gr_batch* b, int32_t* clusters, int32_t* cluster_s
 
 gr_status gr_batch_destroy(gr_batch* b);
 
+/* ---- betweenness centrality (Sec. 6.3) ----------------------------------- */
+
+typedef struct gr_bc_opts {
+  int32_t big_degree;    /* rows at least this long are shared by the grid as
+                            edge chunks in both passes; 0 = default (256)     */
+  int32_t blocks_per_sm; /* persistent grid = blocks_per_sm * SMs; 0 = max    */
+  uint32_t spin_limit;   /* grid-barrier wait budget in polls; 0 = default    */
+  gr_workspace* ws;      /* NULL = the graph's default workspace              */
+} gr_bc_opts;
+
+void gr_bc_opts_default(gr_bc_opts* o);
+
+/*
+ * Brandes' betweenness-centrality pass for one source (Sec. 6.3): a forward
+ * BFS that counts shortest paths, then a backward pass over the BFS levels
+ * that accumulates dependencies.  Outputs (device arrays of n entries, each
+ * may be NULL, then kept in workspace scratch):
+ *   depth[v]: BFS depth from src (-1 unreachable);
+ *   sigma[v]: number of shortest src -> v paths (sigma[src] = 1, 0 when
+ *     unreachable), exact 64-bit integers; a count above INT64_MAX records
+ *     GR_ERR_OVERFLOW in the status word (and the counts are then invalid);
+ *   delta[v]: the dependency of src on v, the sum over edges (v, w) with
+ *     depth[w] = depth[v] + 1 of sigma[v] / sigma[w] * (1 + delta[w]), in
+ *     double precision (the summation order is not fixed: results agree
+ *     with a sequential evaluation to within rounding);
+ *   bc[v] (accumulated): bc[v] += delta[v] for every v != src, so that calls
+ *     for several sources on one array sum the betweenness centrality over
+ *     ordered (source, target) pairs.
+ * Works on directed graphs too (paths follow edge directions).  The first
+ * call on a workspace allocates its BC scratch (about 40 bytes per vertex
+ * plus 8 bytes per 32 edges), kept until the workspace is destroyed.  One
+ * persistent kernel, asynchronous on `stream`.
+ */
+gr_status gr_bc(const gr_graph* g, int32_t src, int32_t* depth, int64_t* sigma, double* delta,
+                double* bc, const gr_bc_opts* opts, void* stream);
+
 /* ---- BFS without allocation --------------------------------------------- */
 
 /*

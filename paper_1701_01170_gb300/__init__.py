@@ -74,6 +74,11 @@ class gr_batch_opts(ctypes.Structure):
                 ("spin_limit", c_u32)]
 
 
+class gr_bc_opts(ctypes.Structure):
+    _fields_ = [("big_degree", c_i32), ("blocks_per_sm", c_i32), ("spin_limit", c_u32),
+                ("ws", c_vp)]
+
+
 class gr_run_stats(ctypes.Structure):
     _fields_ = [("levels", c_i32), ("reserved", c_i32), ("edges", c_i64), ("vertices", c_i64),
                 ("updates", c_i64)]
@@ -117,6 +122,8 @@ _SIGNATURES = {
     "gr_batch_info": ([c_vp, c_vp, c_vp, c_vp], c_i32),
     "gr_batch_destroy": ([c_vp], c_i32),
     "gr_bfs_static": ([c_i32, c_i64, c_vp, c_vp, c_u32, c_i32, c_vp, c_vp, c_vp, c_vp], c_i32),
+    "gr_bc_opts_default": ([ctypes.POINTER(gr_bc_opts)], None),
+    "gr_bc": ([c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(gr_bc_opts), c_vp], c_i32),
 }
 GR_STATIC_MAX_VERTICES = 1 << 20
 GR_STATIC_MAX_EDGES = 1 << 25
@@ -361,6 +368,31 @@ def gr_batch_info(b):
 
 def gr_batch_destroy(b):
     _check(load().gr_batch_destroy(c_vp(b)), "gr_batch_destroy")
+
+
+def bc_opts(**kw) -> gr_bc_opts:
+    return _opts(gr_bc_opts, "gr_bc_opts_default", kw)
+
+
+def _buf(t, count: int, size: int, what: str):
+    """Device pointer of a CUDA tensor of `size`-byte elements holding at least `count`."""
+    if t is None or isinstance(t, int):
+        return _ptr(t)
+    if t.element_size() != size:
+        raise ValueError(f"{what}: expected {8 * size}-bit elements, got {t.dtype}")
+    if t.numel() < count:
+        raise ValueError(f"{what}: needs {count} elements, the tensor has {t.numel()}")
+    return _ptr(t)
+
+
+def gr_bc(g, src, depth=None, sigma=None, delta=None, bc=None, opts=None, stream=None):
+    """Brandes' pass for one source: depth int32, sigma int64, delta float64 (each n or
+    None) and bc float64 (n, accumulated) are CUDA tensors."""
+    n = _graph_n(g)
+    st = load().gr_bc(c_vp(g), src, _buf(depth, n, 4, "depth"), _buf(sigma, n, 8, "sigma"),
+                      _buf(delta, n, 8, "delta"), _buf(bc, n, 8, "bc"),
+                      ctypes.byref(opts) if opts is not None else None, _stream(stream))
+    _check(st, "gr_bc")
 
 
 def gr_bfs_static(n, m, row_offsets, cols, src, depth, pred=None, status=None, flags=0,

@@ -186,6 +186,7 @@ static void ws_free(gr_workspace* ws) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ws->h_status) cudaFreeHost(ws->h_status);
+  gr_bc_free(ws->bc);
   delete ws;
 }
 

@@ -112,6 +112,8 @@ struct GrCounters {
 
 struct GrMsState;                  // multi-source BFS scratch (gr_msbfs.cu)
 void gr_ms_free(GrMsState* ms);
+struct GrBcScratch;                // betweenness-centrality scratch of a workspace (gr_bc.cu)
+void gr_bc_free(GrBcScratch* b);
 
 struct gr_graph {
   int32_t n;
@@ -155,6 +157,7 @@ struct gr_workspace {
   int32_t* tags;        // pull scratch: n entries
   long long* item_off;  // advance scratch: n + 1 per-item output offsets
   long long* dev_len;   // operator scratch: a few device counters
+  GrBcScratch* bc;      // allocated by the first gr_bc call on this workspace
 };
 
 // ---------------------------------------------------------------------------
