@@ -457,6 +457,35 @@ void gr_bc_opts_default(gr_bc_opts* o);
 gr_status gr_bc(const gr_graph* g, int32_t src, int32_t* depth, int64_t* sigma, double* delta,
                 double* bc, const gr_bc_opts* opts, void* stream);
 
+/* ---- connected components (Sec. 6.4) ------------------------------------ */
+
+typedef struct gr_cc_opts {
+  int32_t big_degree;    /* rows at least this long are shared by the grid as
+                            edge chunks in the first hooking pass; 0 = default
+                            (1024)                                           */
+  int32_t blocks_per_sm; /* persistent grid = blocks_per_sm * SMs; 0 = max    */
+  uint32_t spin_limit;   /* grid-barrier wait budget in polls; 0 = default    */
+  gr_workspace* ws;      /* NULL = the graph's default workspace              */
+} gr_cc_opts;
+
+void gr_cc_opts_default(gr_cc_opts* o);
+
+/*
+ * Connected-component labels of a GR_SYMMETRIC graph (Sec. 6.4: hooking on an
+ * edge frontier filtered to the edges whose end points still carry different
+ * labels, then pointer jumping, repeated until no such edge remains).
+ *   comp: device int32[n]; comp[v] = the smallest vertex id of v's component
+ *     (a canonical labelling: equal for two vertices exactly when a path joins
+ *     them).
+ *   num_components: device int32* or NULL; receives the number of components.
+ * Returns GR_ERR_UNSUPPORTED for a graph created without GR_SYMMETRIC.  The
+ * first call on a workspace allocates its CC scratch (about 8 bytes per edge
+ * plus 2 KB per resident warp), kept until the workspace is destroyed.  One
+ * persistent kernel, asynchronous on `stream`.
+ */
+gr_status gr_cc(const gr_graph* g, int32_t* comp, int32_t* num_components,
+                const gr_cc_opts* opts, void* stream);
+
 /* ---- BFS without allocation --------------------------------------------- */
 
 /*

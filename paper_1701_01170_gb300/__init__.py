@@ -79,6 +79,11 @@ class gr_bc_opts(ctypes.Structure):
                 ("ws", c_vp)]
 
 
+class gr_cc_opts(ctypes.Structure):
+    _fields_ = [("big_degree", c_i32), ("blocks_per_sm", c_i32), ("spin_limit", c_u32),
+                ("ws", c_vp)]
+
+
 class gr_run_stats(ctypes.Structure):
     _fields_ = [("levels", c_i32), ("reserved", c_i32), ("edges", c_i64), ("vertices", c_i64),
                 ("updates", c_i64)]
@@ -124,6 +129,8 @@ _SIGNATURES = {
     "gr_bfs_static": ([c_i32, c_i64, c_vp, c_vp, c_u32, c_i32, c_vp, c_vp, c_vp, c_vp], c_i32),
     "gr_bc_opts_default": ([ctypes.POINTER(gr_bc_opts)], None),
     "gr_bc": ([c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(gr_bc_opts), c_vp], c_i32),
+    "gr_cc_opts_default": ([ctypes.POINTER(gr_cc_opts)], None),
+    "gr_cc": ([c_vp, c_vp, c_vp, ctypes.POINTER(gr_cc_opts), c_vp], c_i32),
 }
 GR_STATIC_MAX_VERTICES = 1 << 20
 GR_STATIC_MAX_EDGES = 1 << 25
@@ -393,6 +400,19 @@ def gr_bc(g, src, depth=None, sigma=None, delta=None, bc=None, opts=None, stream
                       _buf(delta, n, 8, "delta"), _buf(bc, n, 8, "bc"),
                       ctypes.byref(opts) if opts is not None else None, _stream(stream))
     _check(st, "gr_bc")
+
+
+def cc_opts(**kw) -> gr_cc_opts:
+    return _opts(gr_cc_opts, "gr_cc_opts_default", kw)
+
+
+def gr_cc(g, comp, num_components=None, opts=None, stream=None):
+    """Component labels (smallest vertex id per component) into comp (int32, n); the
+    component count into num_components (a 1-element int32 CUDA tensor) if given."""
+    n = _graph_n(g)
+    st = load().gr_cc(c_vp(g), _buf(comp, n, 4, "comp"), _buf(num_components, 1, 4, "count"),
+                      ctypes.byref(opts) if opts is not None else None, _stream(stream))
+    _check(st, "gr_cc")
 
 
 def gr_bfs_static(n, m, row_offsets, cols, src, depth, pred=None, status=None, flags=0,

@@ -187,6 +187,7 @@ static void ws_free(gr_workspace* ws) {
     if (p) cudaFree(p);
   if (ws->h_status) cudaFreeHost(ws->h_status);
   gr_bc_free(ws->bc);
+  gr_cc_free(ws->cc);
   delete ws;
 }
 

@@ -114,6 +114,8 @@ struct GrMsState;                  // multi-source BFS scratch (gr_msbfs.cu)
 void gr_ms_free(GrMsState* ms);
 struct GrBcScratch;                // betweenness-centrality scratch of a workspace (gr_bc.cu)
 void gr_bc_free(GrBcScratch* b);
+struct GrCcScratch;                // connected-components scratch of a workspace (gr_cc.cu)
+void gr_cc_free(GrCcScratch* c);
 
 struct gr_graph {
   int32_t n;
@@ -158,6 +160,7 @@ struct gr_workspace {
   long long* item_off;  // advance scratch: n + 1 per-item output offsets
   long long* dev_len;   // operator scratch: a few device counters
   GrBcScratch* bc;      // allocated by the first gr_bc call on this workspace
+  GrCcScratch* cc;      // allocated by the first gr_cc call on this workspace
 };
 
 // ---------------------------------------------------------------------------
