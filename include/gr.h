@@ -486,6 +486,46 @@ void gr_cc_opts_default(gr_cc_opts* o);
 gr_status gr_cc(const gr_graph* g, int32_t* comp, int32_t* num_components,
                 const gr_cc_opts* opts, void* stream);
 
+/* ---- segmented intersection (Sec. 4.3) and triangle counting (Sec. 6.6) -- */
+
+/*
+ * Segmented intersection: for every pair i of the two input frontiers a, b
+ * (device int32[len] each, ids in [0, n)), the ids present in both neighbour
+ * lists N(a[i]) and N(b[i]).  Needs a GR_SYMMETRIC graph (its rows are
+ * validated as strictly increasing, i.e. sorted sets); GR_ERR_UNSUPPORTED
+ * otherwise.  A pair whose ids are not in [0, n) counts as empty and records
+ * GR_ERR_INVALID_ARG in the status word.
+ *   counts: device int64[len] or NULL; counts[i] = |N(a[i]) & N(b[i])|.
+ *   total: device int64 or NULL; the sum of the counts.
+ *   out: device int32[out_cap] or NULL; the intersections in pair order,
+ *     each ascending (the output frontier of Sec. 4.3).  Requires counts and
+ *     out_len (device int64, receives the total even when it exceeds
+ *     out_cap; only out_cap items are written).
+ *   ws: workspace whose scratch is used (NULL = the graph's default); the
+ *     first call allocates the offsets array (8 bytes per pair), grown as
+ *     needed and kept until the workspace is destroyed.
+ * Asynchronous on `stream`.
+ */
+gr_status gr_segmented_intersect(const gr_graph* g, const int32_t* a, const int32_t* b,
+                                 int64_t len, int64_t* counts, int64_t* total, int32_t* out,
+                                 int64_t out_cap, int64_t* out_len, gr_workspace* ws,
+                                 void* stream);
+
+/*
+ * Triangle counting of a GR_SYMMETRIC graph by the forward algorithm of
+ * Sec. 6.6: each undirected edge is kept once, pointing from the end point
+ * with the larger (degree, id) to the other, and every triangle is then the
+ * common out-neighbour of the two ends of exactly one kept edge, found by the
+ * segmented intersection above.
+ *   total: device int64; the number of triangles (each counted once).
+ *   per_vertex: device int64[n] or NULL; per_vertex[v] = the number of
+ *     triangles containing v (costs one atomic per triangle).
+ * The first call on a workspace allocates its scratch (about 14 bytes per
+ * edge), kept until the workspace is destroyed.  Asynchronous on `stream`.
+ */
+gr_status gr_triangle_count(const gr_graph* g, int64_t* total, int64_t* per_vertex,
+                            gr_workspace* ws, void* stream);
+
 /* ---- BFS without allocation --------------------------------------------- */
 
 /*

@@ -131,6 +131,9 @@ _SIGNATURES = {
     "gr_bc": ([c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(gr_bc_opts), c_vp], c_i32),
     "gr_cc_opts_default": ([ctypes.POINTER(gr_cc_opts)], None),
     "gr_cc": ([c_vp, c_vp, c_vp, ctypes.POINTER(gr_cc_opts), c_vp], c_i32),
+    "gr_segmented_intersect": ([c_vp, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp, c_i64, c_vp, c_vp,
+                                c_vp], c_i32),
+    "gr_triangle_count": ([c_vp, c_vp, c_vp, c_vp, c_vp], c_i32),
 }
 GR_STATIC_MAX_VERTICES = 1 << 20
 GR_STATIC_MAX_EDGES = 1 << 25
@@ -413,6 +416,29 @@ def gr_cc(g, comp, num_components=None, opts=None, stream=None):
     st = load().gr_cc(c_vp(g), _buf(comp, n, 4, "comp"), _buf(num_components, 1, 4, "count"),
                       ctypes.byref(opts) if opts is not None else None, _stream(stream))
     _check(st, "gr_cc")
+
+
+def gr_segmented_intersect(g, a, b, length, counts=None, total=None, out=None, out_len=None,
+                           out_cap=None, ws=None, stream=None):
+    """Per-pair neighbour-list intersections; a, b int32 CUDA tensors, counts int64 (length),
+    total / out_len 1-element int64 tensors, out int32 tensor."""
+    cap = out.numel() if out is not None and out_cap is None else (out_cap or 0)
+    st = load().gr_segmented_intersect(c_vp(g), _buf(a, length, 4, "a"), _buf(b, length, 4, "b"),
+                                       length, _buf(counts, length, 8, "counts"),
+                                       _buf(total, 1, 8, "total"), _buf(out, 0, 4, "out"), cap,
+                                       _buf(out_len, 1, 8, "out_len"), c_vp(ws) if ws else None,
+                                       _stream(stream))
+    _check(st, "gr_segmented_intersect")
+
+
+def gr_triangle_count(g, total, per_vertex=None, ws=None, stream=None):
+    """Triangles of a symmetric graph into total (1-element int64 CUDA tensor); optional
+    per-vertex counts (int64, n)."""
+    n = _graph_n(g)
+    st = load().gr_triangle_count(c_vp(g), _buf(total, 1, 8, "total"),
+                                  _buf(per_vertex, n, 8, "per_vertex"), c_vp(ws) if ws else None,
+                                  _stream(stream))
+    _check(st, "gr_triangle_count")
 
 
 def gr_bfs_static(n, m, row_offsets, cols, src, depth, pred=None, status=None, flags=0,

@@ -188,6 +188,7 @@ static void ws_free(gr_workspace* ws) {
   if (ws->h_status) cudaFreeHost(ws->h_status);
   gr_bc_free(ws->bc);
   gr_cc_free(ws->cc);
+  gr_tc_free(ws->tc);
   delete ws;
 }
 

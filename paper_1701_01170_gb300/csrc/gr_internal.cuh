@@ -116,6 +116,8 @@ struct GrBcScratch;                // betweenness-centrality scratch of a worksp
 void gr_bc_free(GrBcScratch* b);
 struct GrCcScratch;                // connected-components scratch of a workspace (gr_cc.cu)
 void gr_cc_free(GrCcScratch* c);
+struct GrTcScratch;                // intersection / triangle scratch of a workspace (gr_tc.cu)
+void gr_tc_free(GrTcScratch* t);
 
 struct gr_graph {
   int32_t n;
@@ -161,6 +163,7 @@ struct gr_workspace {
   long long* dev_len;   // operator scratch: a few device counters
   GrBcScratch* bc;      // allocated by the first gr_bc call on this workspace
   GrCcScratch* cc;      // allocated by the first gr_cc call on this workspace
+  GrTcScratch* tc;      // allocated by the first intersection / triangle call
 };
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,483 @@
+// gr_tc.cu — the segmented-intersection operator (Sec. 4.3) and triangle
+// counting built on it (Sec. 6.6).
+//
+// Segmented intersection: for every input pair (a[i], b[i]) the ids present in
+// both sorted neighbour lists.  Work per pair is the size of its lists, so
+// pairs are grouped as the paper's two kernels do, here inside one warp: each
+// lane takes one pair and, when both lists together hold at most
+// GR_TWO_SMALL ids, merges them alone (TwoSmall); the warp then takes the
+// remaining pairs one at a time, its lanes walking the shorter list 32 ids per
+// round and binary-searching each id in the longer one (SmallLarge).  Counts
+// go to counts[i] and a block-reduced total; with an item output the counts
+// are scanned into offsets and a second pass writes every intersection in
+// pair order, each ascending.
+//
+// Triangle counting follows the forward algorithm the paper describes: every
+// undirected edge is kept once, pointing from the end point with the larger
+// (degree, id) to the one with the smaller, which makes an acyclic graph
+// G+ whose rows stay sorted; a triangle then shows up exactly once, as a
+// common out-neighbour w of the two ends of one G+ edge (u, v).  G+ is built
+// by a scan of keep flags over the CSR in edge order (which preserves each
+// row's order) and a compaction; the count is the segmented intersection of
+// (N+(u), N+(v)) over all G+ edges.
+#include <climits>
+#include <mutex>
+#include <new>
+
+#include "gr_internal.cuh"
+
+struct GrTcScratch {
+  int32_t* src;        // source vertex of every CSR edge (m)
+  int32_t* pos;        // scanned keep flags (m + 1)
+  int32_t* cp;         // G+ columns (m / 2 + 1)
+  int32_t* sp;         // G+ edge sources (m / 2 + 1)
+  int32_t* rp;         // G+ row offsets (n + 1)
+  long long* sums;     // scan block sums
+  int64_t sums_cap;
+  long long* offs;     // intersection offsets of the operator (grown on demand)
+  int64_t offs_cap;
+};
+
+void gr_tc_free(GrTcScratch* t) {
+  if (!t) return;
+  void* ptrs[] = {t->src, t->pos, t->cp, t->sp, t->rp, t->sums, t->offs};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete t;
+}
+
+namespace {
+
+constexpr int T = 256;          // threads per block
+constexpr int ITEMS = 16;       // scan items per thread
+constexpr int TILE = T * ITEMS;
+#ifndef GR_TWO_SMALL
+#define GR_TWO_SMALL 64         // a lane merges a pair alone when its lists hold at most this
+#endif
+
+// ---- device-wide exclusive scan: tiles, then their sums, then the offsets --
+template <class V, class F>
+__global__ void scan_tiles(int64_t count, F value, V* out, long long* sums) {
+  __shared__ long long warp_tot[T / 32];
+  const int64_t base = (int64_t)blockIdx.x * TILE + (int64_t)threadIdx.x * ITEMS;
+  long long x[ITEMS];
+  long long s = 0;
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    x[k] = base + k < count ? (long long)value(base + k) : 0;
+    s += x[k];
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(GR_FULL_MASK, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    long long t = lane < T / 32 ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(GR_FULL_MASK, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < T / 32) warp_tot[lane] = t;
+  }
+  __syncthreads();
+  long long off = (wid ? warp_tot[wid - 1] : 0) + incl - s;
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    if (base + k < count) out[base + k] = (V)off;
+    off += x[k];
+  }
+  if (threadIdx.x == 0) sums[blockIdx.x] = warp_tot[T / 32 - 1];
+}
+
+// One block scans the tile sums in place (exclusive) and writes the total.
+template <class V>
+__global__ void scan_sums(long long* sums, int64_t ntiles, V* total) {
+  __shared__ long long carry;
+  __shared__ long long warp_tot[32];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t b0 = 0; b0 < ntiles; b0 += blockDim.x) {
+    const int64_t i = b0 + threadIdx.x;
+    const long long x = i < ntiles ? sums[i] : 0;
+    long long incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(GR_FULL_MASK, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      long long t = lane < nw ? warp_tot[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(GR_FULL_MASK, t, o);
+        if (lane >= o) t += y;
+      }
+      if (lane < nw) warp_tot[lane] = t;
+    }
+    __syncthreads();
+    const long long excl = carry + (wid ? warp_tot[wid - 1] : 0) + incl - x;
+    if (i < ntiles) sums[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += warp_tot[nw - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = (V)carry;
+}
+
+template <class V>
+__global__ void scan_add(int64_t count, V* out, const long long* sums) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (V)((long long)out[i] + sums[i / TILE]);
+}
+
+// Exclusive scan of value(i), i in [0, count), into out[0 .. count]; out[count]
+// receives the total.  sums needs count / TILE + 1 entries.
+template <class V, class F>
+cudaError_t device_scan(int64_t count, F value, V* out, long long* sums, int sms, cudaStream_t s) {
+  const int64_t ntiles = (count + TILE - 1) / TILE;
+  if (ntiles > 0) scan_tiles<V><<<(unsigned)ntiles, T, 0, s>>>(count, value, out, sums);
+  scan_sums<V><<<1, 1024, 0, s>>>(sums, ntiles, out + count);
+  if (ntiles > 1) scan_add<V><<<sms * 8, T, 0, s>>>(count, out, sums);
+  return cudaGetLastError();
+}
+
+// ---- intersections ----------------------------------------------------------
+
+// Position of the first id >= x in B[0, nb).
+__device__ __forceinline__ int lower_bound_id(const int32_t* __restrict__ B, int nb, int32_t x) {
+  int lo = 0, hi = nb;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(B + mid) < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Lists of one pair: A = C[a0, a1), B = C[b0, b1) of one column array.
+struct PairLists {
+  int a0, na, b0, nb;
+};
+
+// Intersect the lists of each lane's pair: a lane with a short pair merges it
+// alone, then the warp takes the long pairs one by one.  `off` is the lane's
+// pair's output offset; emit(w, off + k) is called for the k-th common id w
+// of a pair (k ascending), by the lane that found it.  Returns the count of
+// the lane's own pair.  All 32 lanes call.
+template <class Emit>
+__device__ __forceinline__ long long warp_intersect(const int32_t* __restrict__ col, bool active,
+                                                    PairLists p, long long off, int lane,
+                                                    Emit&& emit) {
+  long long own = 0;
+  const bool small = active && p.na + p.nb <= GR_TWO_SMALL;
+  if (small) {
+    int x = 0, y = 0;
+    while (x < p.na && y < p.nb) {
+      const int32_t cx = __ldg(col + p.a0 + x), cy = __ldg(col + p.b0 + y);
+      if (cx < cy) ++x;
+      else if (cy < cx) ++y;
+      else {
+        emit(cx, off + own);
+        ++own;
+        ++x;
+        ++y;
+      }
+    }
+  }
+  unsigned big = __ballot_sync(GR_FULL_MASK, active && !small && p.na > 0 && p.nb > 0);
+  while (big) {
+    const int j = __ffs(big) - 1;
+    big &= big - 1u;
+    int s0 = __shfl_sync(GR_FULL_MASK, p.a0, j), ns = __shfl_sync(GR_FULL_MASK, p.na, j);
+    int l0 = __shfl_sync(GR_FULL_MASK, p.b0, j), nl = __shfl_sync(GR_FULL_MASK, p.nb, j);
+    const long long offj = __shfl_sync(GR_FULL_MASK, off, j);
+    if (ns > nl) {  // walk the shorter list, search the longer
+      int t = s0; s0 = l0; l0 = t;
+      t = ns; ns = nl; nl = t;
+    }
+    long long found = 0;  // matches of this pair before the current round
+    for (int i0 = 0; i0 < ns; i0 += 32) {
+      const int i = i0 + lane;
+      bool hit = false;
+      int32_t x = 0;
+      if (i < ns) {
+        x = __ldg(col + s0 + i);
+        const int q = lower_bound_id(col + l0, nl, x);
+        hit = q < nl && __ldg(col + l0 + q) == x;
+      }
+      const unsigned hm = __ballot_sync(GR_FULL_MASK, hit);
+      if (hit) emit(x, offj + found + __popc(hm & ((1u << lane) - 1u)));
+      found += __popc(hm);
+    }
+    if (lane == j) own = found;
+  }
+  return own;
+}
+
+__device__ __forceinline__ void block_add_total(long long mine, unsigned long long* total) {
+  __shared__ long long s_tot;
+  if (threadIdx.x == 0) s_tot = 0;
+  __syncthreads();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(GR_FULL_MASK, mine, o);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd((unsigned long long*)&s_tot, (unsigned long long)mine);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_tot) atomicAdd(total, (unsigned long long)s_tot);
+}
+
+// ---- the operator -----------------------------------------------------------
+
+// Counts (and, with offsets, the items) of the pairs (a[i], b[i]) over the
+// full neighbour lists.  Ids outside [0, n) give empty lists and record
+// GR_ERR_INVALID_ARG.
+__global__ void seg_intersect(int32_t n, const int32_t* __restrict__ R,
+                              const int32_t* __restrict__ C, const int32_t* __restrict__ a,
+                              const int32_t* __restrict__ b, int64_t len, int64_t* counts,
+                              unsigned long long* total, const long long* offs, int32_t* out,
+                              int64_t out_cap, int* status) {
+  const int lane = threadIdx.x & 31;
+  long long mine = 0;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = w0 * 32; base < len; base += nw * 32) {
+    const int64_t i = base + lane;
+    bool active = i < len;
+    PairLists p{0, 0, 0, 0};
+    if (active) {
+      const int32_t x = __ldg(a + i), y = __ldg(b + i);
+      if (x < 0 || x >= n || y < 0 || y >= n) {
+        gr_set_status(status, GR_ERR_INVALID_ARG);
+        active = false;
+      } else {
+        p.a0 = __ldg(R + x);
+        p.na = __ldg(R + x + 1) - p.a0;
+        p.b0 = __ldg(R + y);
+        p.nb = __ldg(R + y + 1) - p.b0;
+      }
+    }
+    const long long o = out && i < len ? offs[i] : 0;
+    const long long c = warp_intersect(C, active, p, o, lane, [&](int32_t w, long long at) {
+      if (out && at < out_cap) out[at] = w;
+    });
+    if (i < len && counts && !out) counts[i] = c;
+    mine += c;
+  }
+  if (total && !out) block_add_total(mine, total);
+}
+
+// ---- triangle counting ------------------------------------------------------
+
+__global__ void tc_sources(int32_t n, const int32_t* __restrict__ R, int32_t* src) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = w0; u < n; u += nw) {
+    const int e0 = __ldg(R + u), e1 = __ldg(R + u + 1);
+    for (int e = e0 + lane; e < e1; e += 32) src[e] = (int32_t)u;
+  }
+}
+
+// Edge (u, v) is kept in G+ when (deg u, u) > (deg v, v).
+struct KeepFlag {
+  const int32_t* R;
+  const int32_t* C;
+  const int32_t* src;
+  __device__ __forceinline__ int operator()(int64_t e) const {
+    const int32_t u = __ldg(src + e), v = __ldg(C + e);
+    const int du = __ldg(R + u + 1) - __ldg(R + u), dv = __ldg(R + v + 1) - __ldg(R + v);
+    return (du > dv || (du == dv && u > v)) ? 1 : 0;
+  }
+};
+
+__global__ void tc_compact(int32_t n, int64_t m, const int32_t* __restrict__ R,
+                           const int32_t* __restrict__ C, const int32_t* __restrict__ src,
+                           const int32_t* __restrict__ pos, int32_t* cp, int32_t* sp, int32_t* rp) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = tid; e < m; e += nth) {
+    const int32_t p = __ldg(pos + e);
+    if (__ldg(pos + e + 1) != p) {  // kept
+      cp[p] = __ldg(C + e);
+      sp[p] = __ldg(src + e);
+    }
+  }
+  for (int64_t u = tid; u <= n; u += nth) rp[u] = __ldg(pos + (u < n ? __ldg(R + u) : m));
+}
+
+__global__ void tc_count(const int32_t* mp_dev, const int32_t* __restrict__ rp,
+                         const int32_t* __restrict__ cp, const int32_t* __restrict__ sp,
+                         unsigned long long* total, unsigned long long* per_vertex) {
+  const int64_t mp = *mp_dev;  // edges of G+ (the scan total)
+  const int lane = threadIdx.x & 31;
+  long long mine = 0;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = w0 * 32; base < mp; base += nw * 32) {
+    const int64_t e = base + lane;
+    const bool active = e < mp;
+    PairLists p{0, 0, 0, 0};
+    int32_t u = 0, v = 0;
+    if (active) {
+      u = __ldg(sp + e);
+      v = __ldg(cp + e);
+      p.a0 = __ldg(rp + u);
+      p.na = __ldg(rp + u + 1) - p.a0;
+      p.b0 = __ldg(rp + v);
+      p.nb = __ldg(rp + v + 1) - p.b0;
+    }
+    const long long c = warp_intersect(cp, active, p, 0ll, lane, [&](int32_t w, long long) {
+      if (per_vertex) atomicAdd(per_vertex + w, 1ull);
+    });
+    if (per_vertex && c) {
+      atomicAdd(per_vertex + u, (unsigned long long)c);
+      atomicAdd(per_vertex + v, (unsigned long long)c);
+    }
+    mine += c;
+  }
+  block_add_total(mine, total);
+}
+
+std::mutex g_tc_mu;
+
+gr_status tc_scratch(const gr_graph* g, gr_workspace* ws, int64_t offs_need, GrTcScratch** out) {
+  std::lock_guard<std::mutex> lock(g_tc_mu);
+  GrTcScratch* t = ws->tc;
+  if (!t) {
+    t = new (std::nothrow) GrTcScratch();
+    if (!t) return GR_ERR_OOM;
+    ws->tc = t;
+  }
+  const int64_t m = g->m, n = g->n;
+  auto grow = [&](void** p, size_t bytes) {
+    return cudaMalloc(p, bytes) == cudaSuccess;
+  };
+  if (!t->sums) {
+    t->sums_cap = (m > n ? m : n) / TILE + 8;
+    if (!grow((void**)&t->sums, (size_t)t->sums_cap * sizeof(long long))) goto oom;
+  }
+  if (offs_need > t->offs_cap) {
+    if (t->offs) cudaFree(t->offs);
+    t->offs = nullptr;
+    t->offs_cap = 0;
+    if (!grow((void**)&t->offs, (size_t)offs_need * sizeof(long long))) goto oom;
+    t->offs_cap = offs_need;
+    if ((offs_need + TILE - 1) / TILE + 2 > t->sums_cap) {
+      cudaFree(t->sums);
+      t->sums_cap = offs_need / TILE + 8;
+      if (!grow((void**)&t->sums, (size_t)t->sums_cap * sizeof(long long))) { t->sums = nullptr; goto oom; }
+    }
+  }
+  *out = t;
+  return GR_OK;
+oom:
+  (void)cudaGetLastError();
+  return GR_ERR_OOM;
+}
+
+gr_status tc_graph_scratch(const gr_graph* g, GrTcScratch* t) {
+  std::lock_guard<std::mutex> lock(g_tc_mu);
+  if (t->src) return GR_OK;
+  const size_t m = (size_t)g->m, n = (size_t)g->n;
+  bool ok = cudaMalloc((void**)&t->src, (m + 1) * sizeof(int32_t)) == cudaSuccess &&
+            cudaMalloc((void**)&t->pos, (m + 1) * sizeof(int32_t)) == cudaSuccess &&
+            cudaMalloc((void**)&t->cp, (m / 2 + 2) * sizeof(int32_t)) == cudaSuccess &&
+            cudaMalloc((void**)&t->sp, (m / 2 + 2) * sizeof(int32_t)) == cudaSuccess &&
+            cudaMalloc((void**)&t->rp, (n + 1) * sizeof(int32_t)) == cudaSuccess;
+  if (!ok) {
+    (void)cudaGetLastError();
+    void* ptrs[] = {t->src, t->pos, t->cp, t->sp, t->rp};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+    t->src = t->pos = t->cp = t->sp = t->rp = nullptr;
+    return GR_ERR_OOM;
+  }
+  return GR_OK;
+}
+
+}  // namespace
+
+extern "C" gr_status gr_segmented_intersect(const gr_graph* g, const int32_t* a, const int32_t* b,
+                                            int64_t len, int64_t* counts, int64_t* total,
+                                            int32_t* out, int64_t out_cap, int64_t* out_len,
+                                            gr_workspace* ws, void* stream) {
+  if (!g || len < 0 || (len > 0 && (!a || !b)) || (out && (!counts || !out_len || out_cap < 0)))
+    return GR_ERR_INVALID_ARG;
+  if (!(g->flags & GR_SYMMETRIC)) return GR_ERR_UNSUPPORTED;  // rows must be sorted sets
+  ws = gr_resolve_ws(g, ws);
+  if (!ws || ws->g != g) return GR_ERR_INVALID_ARG;
+  GrTcScratch* t = nullptr;
+  gr_status st = tc_scratch(g, ws, out ? len + 1 : 0, &t);
+  if (st != GR_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int blocks = g->num_sms * 8;
+  if (total && cudaMemsetAsync(total, 0, sizeof(int64_t), s) != cudaSuccess) goto cuda_err;
+  if (len == 0) {
+    if (out_len && cudaMemsetAsync(out_len, 0, sizeof(int64_t), s) != cudaSuccess) goto cuda_err;
+    return GR_OK;
+  }
+  seg_intersect<<<blocks, T, 0, s>>>(g->n, g->R, g->C, a, b, len, counts,
+                                      (unsigned long long*)total, nullptr, nullptr, 0, ws->status);
+  if (cudaGetLastError() != cudaSuccess) goto cuda_err;
+  if (out) {
+    // offsets of every pair's items, then the items themselves
+    const int64_t* cnt = counts;
+    auto value = [cnt] __device__(int64_t i) -> long long { return (long long)cnt[i]; };
+    if (device_scan<long long>(len, value, t->offs, t->sums, g->num_sms, s) != cudaSuccess)
+      goto cuda_err;
+    seg_intersect<<<blocks, T, 0, s>>>(g->n, g->R, g->C, a, b, len, nullptr, nullptr, t->offs,
+                                        out, out_cap, ws->status);
+    if (cudaGetLastError() != cudaSuccess) goto cuda_err;
+    if (cudaMemcpyAsync(out_len, t->offs + len, sizeof(int64_t), cudaMemcpyDeviceToDevice, s) !=
+        cudaSuccess)
+      goto cuda_err;
+  }
+  return GR_OK;
+cuda_err:
+  (void)cudaGetLastError();
+  return GR_ERR_CUDA;
+}
+
+extern "C" gr_status gr_triangle_count(const gr_graph* g, int64_t* total, int64_t* per_vertex,
+                                       gr_workspace* ws, void* stream) {
+  if (!g || !total) return GR_ERR_INVALID_ARG;
+  if (!(g->flags & GR_SYMMETRIC)) return GR_ERR_UNSUPPORTED;
+  ws = gr_resolve_ws(g, ws);
+  if (!ws || ws->g != g) return GR_ERR_INVALID_ARG;
+  GrTcScratch* t = nullptr;
+  gr_status st = tc_scratch(g, ws, 0, &t);
+  if (st != GR_OK) return st;
+  st = tc_graph_scratch(g, t);
+  if (st != GR_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int blocks = g->num_sms * 8;
+  const int64_t m = g->m;
+  if (cudaMemsetAsync(total, 0, sizeof(int64_t), s) != cudaSuccess) goto cuda_err;
+  if (per_vertex && cudaMemsetAsync(per_vertex, 0, (size_t)g->n * sizeof(int64_t), s) != cudaSuccess)
+    goto cuda_err;
+  if (m == 0) return GR_OK;
+  {
+    // G+: source of every edge, keep flags scanned in edge order, compaction
+    tc_sources<<<blocks, T, 0, s>>>(g->n, g->R, t->src);
+    if (cudaGetLastError() != cudaSuccess) goto cuda_err;
+    KeepFlag keep{g->R, g->C, t->src};
+    if (device_scan<int32_t>(m, keep, t->pos, t->sums, g->num_sms, s) != cudaSuccess)
+      goto cuda_err;
+    tc_compact<<<blocks, T, 0, s>>>(g->n, m, g->R, g->C, t->src, t->pos, t->cp, t->sp, t->rp);
+    if (cudaGetLastError() != cudaSuccess) goto cuda_err;
+    tc_count<<<blocks, T, 0, s>>>(t->pos + m, t->rp, t->cp, t->sp, (unsigned long long*)total,
+                                   (unsigned long long*)per_vertex);
+    if (cudaGetLastError() != cudaSuccess) goto cuda_err;
+  }
+  return GR_OK;
+cuda_err:
+  (void)cudaGetLastError();
+  return GR_ERR_CUDA;
+}
