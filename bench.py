@@ -53,7 +53,7 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--workload", choices=["s22", "s16", "grid", "msbfs", "batch", "serve", "ops",
-                                          "push"],
+                                          "push", "bc", "cc", "tc"],
                    default="s22",
                    help="s22 (default, the headline workload) or one of the other configurations")
     p.add_argument("--rates", default="20,2000,5000,10000,20000,50000",
@@ -513,6 +513,10 @@ def run_ours(args):
     if rank == 0 and not args.no_extras:
         out["push_bfs"] = measure_push_bfs(gr, G, g, timed, depth, flush, hbm, peak_note,
                                            traffic.get("push_bfs"), deg_t, stream)
+        # the next operator families on the same graph (Sec. 6.3, 6.4, 6.6)
+        out["bc"] = measure_bc(gr, G, g, srcs[:4], flush, deg_t, hbm, peak_note)
+        out["cc"] = measure_cc(gr, G, g, hub, flush, hbm, peak_note)
+        out["tc"] = measure_tc(gr, G, g, flush, hbm, peak_note)
     gr.gr_workspace_destroy(ws_bfs)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(g, srcs)
@@ -589,6 +593,104 @@ def measure_push_bfs(gr, G, g, sources, do_depth, flush, hbm, peak_note, traffic
             "achieved": tot_b / (tot_ms / 1e3) / 1e9, "peak": hbm,
             "frac": tot_b / (tot_ms / 1e3) / 1e9 / hbm, "first_source": hub,
             "depths_identical_to_direction_optimising": same, "first_source_levels": trace}
+
+
+def _timed(fn, flush, reps):
+    """CUDA-event times of fn() (ms), each after an untimed L2 flush."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = []
+    for _ in range(reps):
+        flush.zero_()
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def measure_bc(gr, G, g, sources, flush, deg_t, hbm, peak_note):
+    """Brandes' pass (gr_bc) per source.  Algorithmic bytes per source:
+    8 m_r (the columns of the reached rows, read by both passes) + 52 n_r (per reached
+    vertex: BFS-order entry written and read twice, row offsets twice, sigma read twice,
+    delta written) + 44 n (depth, sigma and delta initialised; bc read and written, delta
+    read).  Depths must equal gr_bfs's."""
+    import torch
+    n = g.n
+    depth = torch.empty(n, dtype=torch.int32, device="cuda")
+    sigma = torch.empty(n, dtype=torch.int64, device="cuda")
+    delta = torch.empty(n, dtype=torch.float64, device="cuda")
+    bc = torch.zeros(n, dtype=torch.float64, device="cuda")
+    ref = torch.empty_like(depth)
+    gr.gr_bc(G.handle, sources[0], depth, sigma, delta, bc)          # warm (allocates scratch)
+    tot_ms, tot_b, tot_e, same, per = 0.0, 0, 0, True, []
+    for src in sources:
+        ms = statistics.median(_timed(lambda: gr.gr_bc(G.handle, src, depth, sigma, delta, bc),
+                                      flush, 3))
+        r = depth >= 0
+        m_r, n_r = int((deg_t * r).sum().item()), int(r.sum().item())
+        gr.gr_bfs(G.handle, src, ref, None)
+        same = same and bool(torch.equal(depth, ref))
+        b = 8 * m_r + 52 * n_r + 44 * n
+        tot_ms += ms
+        tot_b += b
+        tot_e += 2 * m_r
+        per.append({"source": int(src), "ms": ms, "m_r": m_r, "n_r": n_r,
+                    "levels": gr.gr_last_run_stats(G.handle)["levels"]})
+    ok = G.sync_status() == gr.GR_OK
+    ach = tot_b / (tot_ms / 1e3) / 1e9
+    return {"kernel": "bc_persistent", "sources": len(sources), "ms_mean": tot_ms / len(sources),
+            "gteps": tot_e / (tot_ms / 1e3) / 1e9,
+            "formula": "8 m_r + 52 n_r + 44 n per source (edges counted twice: both passes)",
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                         "frac": ach / hbm, "traffic": None, "peak_kind": peak_note},
+            "per_source": per, "depths_identical_to_bfs": same and ok}
+
+
+def measure_cc(gr, G, g, hub, flush, hbm, peak_note):
+    """Connected components (gr_cc).  Algorithmic bytes: 4 m (columns once) + 8 n (row
+    offsets and labels) + 16 per hooked edge (written to and read from the filtered edge
+    frontier as an 8-byte pair).  The hub's component must have as many vertices as a BFS
+    from the hub reaches."""
+    import torch
+    comp = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    k = torch.zeros(1, dtype=torch.int32, device="cuda")
+    gr.gr_cc(G.handle, comp, k)                                     # warm (allocates scratch)
+    ms = statistics.median(_timed(lambda: gr.gr_cc(G.handle, comp, k), flush, 3))
+    st = gr.gr_last_run_stats(G.handle)
+    d = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    gr.gr_bfs(G.handle, hub, d, None)
+    ok = G.sync_status() == gr.GR_OK and \
+        int((comp == comp[hub]).sum().item()) == int((d >= 0).sum().item())
+    b = 4 * g.m + 8 * g.n + 16 * st["updates"]
+    ach = b / (ms / 1e3) / 1e9
+    return {"kernel": "cc_persistent", "ms": ms, "components": int(k.item()),
+            "hooking_iterations": st["levels"], "hooked_edges": st["updates"],
+            "gteps": g.m / (ms / 1e3) / 1e9,
+            "formula": "4 m + 8 n + 16 per hooked edge",
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                         "frac": ach / hbm, "traffic": None, "peak_kind": peak_note},
+            "hub_component_matches_bfs": ok}
+
+
+def measure_tc(gr, G, g, flush, hbm, peak_note):
+    """Triangle counting (gr_triangle_count, forward algorithm).  Streamed bytes: 12 m (the
+    CSR columns read to orient the edges, the oriented graph's m/2 (source, column) pairs
+    written and read); the intersections themselves re-read those rows from L2."""
+    import torch
+    total = torch.zeros(1, dtype=torch.int64, device="cuda")
+    gr.gr_triangle_count(G.handle, total)                           # warm (allocates scratch)
+    ms = statistics.median(_timed(lambda: gr.gr_triangle_count(G.handle, total), flush, 3))
+    ok = G.sync_status() == gr.GR_OK
+    b = 12 * g.m
+    ach = b / (ms / 1e3) / 1e9
+    return {"kernel": "tc_count (with tc_sources, scan, tc_compact)", "ms": ms,
+            "triangles": int(total.item()), "triangles_per_s": int(total.item()) / (ms / 1e3),
+            "oriented_edges_per_s": (g.m // 2) / (ms / 1e3),
+            "formula": "12 m streamed", "status_ok": ok,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                         "frac": ach / hbm, "traffic": None, "peak_kind": peak_note}}
 
 
 def run_e2e(gr, g, srcs, args, dev, rank):
@@ -856,6 +958,27 @@ def run_other(args):
               "config": {"workload": "rmat_s22_ef16_seed2: push-only BFS from the highest-degree "
                                      "vertex, then the seeded random sources"},
               "roofline": r["first_source"], **r})
+        return
+    if args.workload in ("bc", "cc", "tc"):
+        # one operator family on R-MAT s22 (the s22 line's bc / cc / tc legs on their own)
+        g, srcs = workload(22)
+        G = gr.Graph.from_csr(g)
+        hbm, peak_note = hbm_peak()
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+        deg_t = torch.from_numpy(g.degrees().astype(np.int64)).cuda()
+        if args.workload == "bc":
+            r = measure_bc(gr, G, g, srcs[:max(1, args.steps)], flush, deg_t, hbm, peak_note)
+            val, unit, ms = r["gteps"], "GTEPS", r["ms_mean"]
+        elif args.workload == "cc":
+            r = measure_cc(gr, G, g, srcs[0], flush, hbm, peak_note)
+            val, unit, ms = r["gteps"], "GTEPS", r["ms"]
+        else:
+            r = measure_tc(gr, G, g, flush, hbm, peak_note)
+            val, unit, ms = r["triangles_per_s"], "triangles/s", r["ms"]
+        G.close()
+        emit({"metric": unit, "value": val, "unit": unit, **base, "ms_per_step": ms,
+              "higher_is_better": True,
+              "config": {"workload": f"rmat_s22_ef16_seed2: {args.workload}"}, **r})
         return
     if args.workload == "msbfs":
         r = measure_msbfs(gr, reps=args.steps)

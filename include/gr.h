@@ -513,10 +513,11 @@ gr_status gr_segmented_intersect(const gr_graph* g, const int32_t* a, const int3
 
 /*
  * Triangle counting of a GR_SYMMETRIC graph by the forward algorithm of
- * Sec. 6.6: each undirected edge is kept once, pointing from the end point
- * with the larger (degree, id) to the other, and every triangle is then the
- * common out-neighbour of the two ends of exactly one kept edge, found by the
- * segmented intersection above.
+ * Sec. 6.6: each undirected edge is kept once, oriented by the (degree, id)
+ * order of its end points (toward the larger end, which keeps every
+ * out-list short), and every triangle is then the common out-neighbour of
+ * the two ends of exactly one kept edge, found by the segmented intersection
+ * above.
  *   total: device int64; the number of triangles (each counted once).
  *   per_vertex: device int64[n] or NULL; per_vertex[v] = the number of
  *     triangles containing v (costs one atomic per triangle).
