@@ -319,6 +319,12 @@ typedef struct gr_sssp_opts {
                             edge.  0 = default (n / 64, at least 4096),
                             < 0 = never                                      */
   int32_t max_blocks;    /* as in gr_bfs_opts                                  */
+  int32_t levels;        /* buckets of the priority queue (Sec. 5.1.5): 0 =
+                            default, the multi-level queue of 8 (the current
+                            bucket and the 7 after it keep lists of their own,
+                            filled by a multisplit of the far pile); 2 = the
+                            two-level near/far queue.  Results do not depend
+                            on it                                             */
 } gr_sssp_opts;
 
 void gr_sssp_opts_default(gr_sssp_opts* o);

@@ -49,7 +49,7 @@ class gr_bfs_opts(ctypes.Structure):
 class gr_sssp_opts(ctypes.Structure):
     _fields_ = [("delta", c_u32), ("big_degree", c_i32), ("blocks_per_sm", c_i32),
                 ("spin_limit", c_u32), ("ws", c_vp), ("level_stats", c_vp), ("max_levels", c_i32),
-                ("bulk_rows", c_i32), ("max_blocks", c_i32)]
+                ("bulk_rows", c_i32), ("max_blocks", c_i32), ("levels", c_i32)]
 
 
 class gr_bfs_state(ctypes.Structure):

@@ -171,7 +171,7 @@ static size_t ws_bytes(const gr_graph* g, int32_t ops) {
   b += (GR_MAX_SCAN_BLOCKS + 2) * sizeof(long long);             // scan scratch
   b += n * sizeof(int32_t) + 8 * sizeof(long long);              // pull tags, counters
   b += n * sizeof(long long);                                    // advance offsets
-  if (ops & GR_OP_SSSP) b += n * sizeof(uint64_t) + 4 * n * sizeof(int32_t);
+  if (ops & GR_OP_SSSP) b += n * sizeof(uint64_t) + (5 + GR_RING_K) * n * sizeof(int32_t);
   return b;
 }
 
@@ -185,6 +185,9 @@ static void ws_free(gr_workspace* ws) {
                   ws->claim, ws->block_sums, ws->tags, ws->item_off, ws->dev_len};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (int j = 0; j < GR_RING_K; ++j)
+    if (ws->ring[j]) cudaFree(ws->ring[j]);
+  if (ws->stamp_ring) cudaFree(ws->stamp_ring);
   if (ws->h_status) cudaFreeHost(ws->h_status);
   gr_bc_free(ws->bc);
   gr_cc_free(ws->cc);
@@ -237,6 +240,8 @@ static gr_status ws_create(const gr_graph* g, int32_t ops, gr_workspace** out) {
     ALLOC(ws->far[1], n * sizeof(int32_t));
     ALLOC(ws->stamp_near, n * sizeof(int32_t));
     ALLOC(ws->stamp_far, n * sizeof(int32_t));
+    for (int j = 0; j < GR_RING_K; ++j) ALLOC(ws->ring[j], n * sizeof(int32_t));
+    ALLOC(ws->stamp_ring, n * sizeof(uint32_t));
   }
 #undef ALLOC
   if (cudaMallocHost((void**)&ws->h_status, sizeof(int)) != cudaSuccess) {

@@ -53,6 +53,13 @@
 #define GR_SCAN_TILE (GR_OPS_THREADS * GR_SCAN_ITEMS)
 #define GR_MAX_SCAN_BLOCKS ((int64_t)1 << 19)  // covers in_len < 2^31
 
+// Buckets of the SSSP multi-level priority queue: the current one and the
+// GR_RING_K - 1 after it have lists of their own (a ring), farther ones share
+// the far pile.
+#ifndef GR_RING_K
+#define GR_RING_K 8
+#endif
+
 // Device control block of a workspace.  The barrier and the per-level
 // counters are cleared by the host (cudaMemsetAsync) before every persistent
 // launch; the status word lives separately and persists until read.
@@ -73,6 +80,7 @@ struct GrCtl {
   int qmlen[3];                    // medium-row queue length, slot = step % 3
   int workm[3];                    // dynamic work counter (medium-row batches)
   unsigned farmin[3];              // SSSP smallest distance pushed to a far pile
+  int rlen[GR_RING_K];             // SSSP multi-level queue: entries of each ring slot
   int ovf_pending;                 // SSSP: some relaxation sum did not fit in 32 bits
   unsigned long long mf[3];        // sum of degrees of the next frontier
   unsigned long long edges;        // column entries read (statistics)
@@ -155,6 +163,8 @@ struct gr_workspace {
   int32_t* far[2];      // SSSP far piles (ping-pong), n entries each
   int32_t* stamp_near;  // SSSP near-queue membership stamps
   int32_t* stamp_far;   // SSSP far-pile membership stamps
+  int32_t* ring[GR_RING_K];  // SSSP multi-level queue: bucket lists, n entries each
+  uint32_t* stamp_ring; // SSSP: last bucket each vertex was added to
   int32_t* first_idx;   // filter scratch: n entries, INT32_MAX when clean
   uint32_t* claim;      // filter scratch: n bits, 0 when clean
   long long* block_sums;// operator scan scratch, GR_MAX_SCAN_BLOCKS + 2 entries

@@ -64,6 +64,7 @@ extern "C" void gr_sssp_opts_default(gr_sssp_opts* o) {
   o->max_levels = 0;
   o->bulk_rows = 0;
   o->max_blocks = 0;
+  o->levels = 0;
 }
 
 // Bucket width from the graph: 256 * mean weight / mean degree, at least 1
@@ -77,7 +78,8 @@ extern "C" gr_status gr_sssp(const gr_graph* g, int32_t src, uint32_t* dist, int
   gr_sssp_opts o;
   gr_sssp_opts_default(&o);
   if (opts) o = *opts;
-  if (o.max_levels < 0 || (o.max_levels > 0 && !o.level_stats) || o.max_blocks < 0)
+  if (o.max_levels < 0 || (o.max_levels > 0 && !o.level_stats) || o.max_blocks < 0 ||
+      (o.levels != 0 && o.levels != 2 && o.levels != GR_RING_K))
     return GR_ERR_INVALID_ARG;
   gr_workspace* ws = gr_resolve_ws(g, o.ws);
   if (!ws || ws->g != g || !ws->key) return GR_ERR_INVALID_ARG;
@@ -113,6 +115,10 @@ extern "C" gr_status gr_sssp(const gr_graph* g, int32_t src, uint32_t* dist, int
   a.spin = o.spin_limit ? o.spin_limit : GR_DEFAULT_SPIN_LIMIT;
   a.level_stats = o.level_stats;
   a.max_levels = o.max_levels;
+  if (o.levels != 2) {
+    for (int j = 0; j < GR_RING_K; ++j) a.ring[j] = ws->ring[j];
+    a.stamp_ring = ws->stamp_ring;
+  }
 
   const bool wide = g->max_degree >= GR_MEDIUM_DEGREE;
   const void* kernel = wide ? (const void*)sssp_persistent<NT_WIDE>

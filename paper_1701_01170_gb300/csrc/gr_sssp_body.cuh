@@ -55,6 +55,12 @@ struct SsspArgs {
   unsigned spin;
   int32_t* level_stats;
   int32_t max_levels;
+  // Multi-level priority queue (NULL: the two-level near/far queue): ring[j]
+  // holds the vertices of bucket b = dist / delta with b % GR_RING_K == j for
+  // the GR_RING_K - 1 buckets after the current one; stamp_ring[v] is the last
+  // bucket v was added to.  Needs the large staging buffers.
+  int32_t* ring[GR_RING_K];
+  uint32_t* stamp_ring;
 };
 
 constexpr unsigned long long GR_KEY_INF = ~0ull;
@@ -78,6 +84,7 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
     a.key[v] = v == a.src ? 0xffffffffull : GR_KEY_INF;
     a.stamp_near[v] = v == a.src ? 0 : -1;
     a.stamp_far[v] = -1;
+    if (a.stamp_ring) a.stamp_ring[v] = UINT_MAX;
   }
   const int nwords = (int)(((int64_t)a.n + 31) >> 5);
   if (a.touched)
@@ -98,6 +105,11 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
   const unsigned long long deadline = gr_globaltimer() + GR_TIME_LIMIT_NS;
   unsigned long long T = a.delta;  // near iff dist < T
   int fe = 0;                      // far-pile epoch
+  // multi-level queue: the current bucket is T / delta - 1; ring_left counts the
+  // ring slots known to hold entries, reset_slot is the slot drained by the
+  // last SPLIT step (its length is cleared at the start of the next step)
+  int ring_left = 0;
+  int reset_slot = -1;
   int it = 0;                      // near step
   GrCounters cnt;
   bool ovf_seen = false;
@@ -138,7 +150,11 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
     const int nrows = nq + nqm + nch;  // zero: a SPLIT step
     const int flen = min(s_flen, a.n);
     const unsigned fm_step = s_fm;
-    if (nrows == 0 && flen == 0) break;
+    if (nrows == 0 && flen == 0 && ring_left == 0) break;
+    if (reset_slot >= 0) {
+      if (gtid == 0) ctl->rlen[reset_slot] = 0;
+      reset_slot = -1;
+    }
     if (gtid == 0) {
       if ((it & 63) == 0) gr_check_deadline(ctl, a.status, deadline);
       if (a.level_stats && it < a.max_levels) {
@@ -354,6 +370,142 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
                                       (int)nwarps, lane, a.R, a.C, cnt, label, pre, relax);
       gr_rows_loop<GR_RELAX_STRIPS>(q, nq, 32, &ctl->work[s0], swarp, (int)nwarps, lane, a.R, a.C,
                                     cnt, label, pre, relax);
+    } else if (a.ring[0] && big) {
+      // ---- SPLIT with the multi-level queue (a multisplit of the far pile) --
+      // Phase 1: every entry of the far pile (vertices that left the current
+      // bucket since the last SPLIT) goes, by its bucket b = dist / delta, to
+      // ring slot b % K when b lies in the window (cb, cb + K) — once per
+      // bucket, by stamp — or to the next far pile; entries whose distance
+      // fell back into an earlier bucket were expanded then and are dropped.
+      // Phase 2: the smallest bucket of the window with entries becomes the
+      // current one and its slot is drained into the near frontier (stale
+      // entries dropped); with an empty window the threshold jumps to the far
+      // pile's smallest distance and the next step splits again.
+      constexpr int K = GR_RING_K;
+      const unsigned long long cb = T / a.delta - 1;
+      if (gtid == 0) {
+        ctl->farlen[(fe + 2) % 3] = 0;
+        ctl->farmin[(fe + 2) % 3] = UINT_MAX;
+      }
+      __shared__ int s_rcnt[K], s_rbase[K], s_rcur[K];
+      __shared__ int s_rn;
+      // staging of this CTA's ring entries: vertex ids in the near buffer and
+      // their slots as bytes in the middle buffer (both idle in this phase)
+      constexpr int RCAP = GR_BIG_NEAR_CAP;
+      static_assert(GR_BIG_MID_CAP * 4 >= RCAP, "slot bytes must fit the middle buffer");
+      int* rv = big->near;
+      unsigned char* rs = (unsigned char*)big->mid;
+      if (threadIdx.x < K) {
+        s_rcnt[threadIdx.x] = 0;
+        s_rcur[threadIdx.x] = 0;
+      }
+      if (threadIdx.x == 0) s_rn = 0;
+      __syncthreads();
+      const int32_t* fp = a.far[fe & 1];
+      for (int base = swarp * 32; base < flen;
+           base = gr_next_batch(base, flen, (int)nwarps * 32, &ctl->work[s0], 32, lane)) {
+        const int i = base + lane;
+        int32_t v = 0;
+        unsigned long long b = 0;
+        const bool valid = i < flen;
+        if (valid) {
+          ++cnt.verts;
+          v = __ldcg(fp + i);
+          b = (__ldcg(a.key + v) >> 32) / a.delta;
+        }
+        bool to_ring = valid && b > cb && b < cb + K;
+        if (to_ring) to_ring = atomicExch(&a.stamp_ring[v], (uint32_t)b) != (uint32_t)b;
+        const unsigned rm = __ballot_sync(GR_FULL_MASK, to_ring);
+        if (rm) {
+          int pos = 0;
+          if (lane == __ffs(rm) - 1) pos = atomicAdd(&s_rn, __popc(rm));
+          pos = __shfl_sync(GR_FULL_MASK, pos, __ffs(rm) - 1) + __popc(rm & ((1u << lane) - 1u));
+          const int j = (int)(b % K);
+          const bool staged = to_ring && pos < RCAP;
+          if (staged) {
+            rv[pos] = v;
+            rs[pos] = (unsigned char)j;
+            atomicAdd(&s_rcnt[j], 1);
+          }
+          // staging full: straight to the ring, one global atomic per warp and slot
+          const bool direct = to_ring && !staged;
+          if (__any_sync(GR_FULL_MASK, direct)) {
+#pragma unroll
+            for (int jj = 0; jj < K; ++jj) {
+              const unsigned dm = __ballot_sync(GR_FULL_MASK, direct && j == jj);
+              if (!dm) continue;
+              int g = 0;
+              if (lane == __ffs(dm) - 1) g = atomicAdd(&ctl->rlen[jj], __popc(dm));
+              g = __shfl_sync(GR_FULL_MASK, g, __ffs(dm) - 1) + __popc(dm & ((1u << lane) - 1u));
+              if (direct && j == jj && g < a.n) a.ring[jj][g] = v;
+            }
+          }
+        }
+        const unsigned long long d = valid ? (__ldcg(a.key + v) >> 32) : 0ull;
+        to_far(valid && b >= cb + K, v, (unsigned)d, fe + 1);
+      }
+      // flush the staged ring entries (one global atomic per CTA and slot) and
+      // the next far pile
+      __syncthreads();
+      if (threadIdx.x < K && s_rcnt[threadIdx.x])
+        s_rbase[threadIdx.x] = atomicAdd(&ctl->rlen[threadIdx.x], s_rcnt[threadIdx.x]);
+      far_stage.reserve(&ctl->farlen[(fe + 1) % 3]);
+      if (threadIdx.x == 0 && s_farmin != UINT_MAX)
+        atomicMin(&ctl->farmin[(fe + 1) % 3], s_farmin);
+      __syncthreads();
+      const int rn = min(s_rn, RCAP);
+      for (int k = threadIdx.x; k < rn; k += blockDim.x) {
+        const int j = rs[k];
+        const int g = s_rbase[j] + atomicAdd(&s_rcur[j], 1);
+        if (g < a.n) a.ring[j][g] = rv[k];
+      }
+      far_stage.copy_out(a.far[(fe + 1) & 1], a.n);
+      __syncthreads();  // every thread has read the stage count before it is cleared
+      if (threadIdx.x == 0) {
+        far_stage.reset();
+        s_farmin = UINT_MAX;
+      }
+      if (!sc.sync()) return;
+      // phase 2: pick the next bucket from the (now stable) slot lengths
+      __shared__ int s_rl[K];
+      __shared__ int s_fl2;
+      __shared__ unsigned s_fm2;
+      if (threadIdx.x < K) s_rl[threadIdx.x] = __ldcg(&ctl->rlen[threadIdx.x]);
+      if (threadIdx.x == 0) {
+        s_fl2 = __ldcg(&ctl->farlen[(fe + 1) % 3]);
+        s_fm2 = __ldcg(&ctl->farmin[(fe + 1) % 3]);
+      }
+      __syncthreads();
+      int nk = 0;  // the next bucket is cb + nk (0: none in the window)
+      for (int k = 1; k < K && !nk; ++k)
+        if (s_rl[(cb + k) % K] > 0) nk = k;
+      ring_left = 0;
+      for (int k = 1; k < K; ++k) ring_left += k != nk && s_rl[(cb + k) % K] > 0;
+      if (nk) {
+        const unsigned long long nb = cb + nk;
+        const int j = (int)(nb % K);
+        const int rl = min(s_rl[j], a.n);
+        for (int base = swarp * 32; base < rl;
+             base = gr_next_batch(base, rl, (int)nwarps * 32, &ctl->workb[s0], 32, lane)) {
+          const int i = base + lane;
+          int32_t v = 0;
+          bool take = false;
+          if (i < rl) {
+            v = __ldcg(a.ring[j] + i);
+            take = (__ldcg(a.key + v) >> 32) / a.delta == nb;
+          }
+          near_append(take, v);
+        }
+        T = (nb + 1) * a.delta;
+        reset_slot = j;
+      } else if (s_fl2 > 0 && s_fm2 != UINT_MAX) {
+        // nothing in the window: the next SPLIT starts the window at the far
+        // pile's smallest distance
+        const unsigned long long fb = (unsigned long long)s_fm2 / a.delta;
+        T = fb * a.delta;  // current bucket fb - 1: the window (fb - 1, fb - 1 + K)
+        if (T == 0) T = a.delta;
+      }
+      ++fe;
     } else {
       // ---- SPLIT: raise the threshold, move far entries below it to near --
       const unsigned fm = fm_step;

@@ -1,4 +1,5 @@
-"""GPU parity of gr_sssp (persistent near/far SSSP) against the CPU oracle.
+"""GPU parity of gr_sssp (persistent SSSP with a multi-level or near/far priority queue)
+against the CPU oracle.
 
 Distances must equal Dijkstra's bit for bit.  Predecessors are the
 smallest-id tight predecessor (the packed 64-bit atomicMin makes them
@@ -47,11 +48,13 @@ def s16w(gr):
     return g, gr.Graph.from_csr(g)
 
 
-@pytest.mark.parametrize("delta", [0, 1, 7, 64, 1 << 30])
-def test_rmat_s16_deltas_agree(gr, s16w, delta):
+@pytest.mark.parametrize("delta", [0, 1, 2, 4, 7, 64, 1 << 30])
+@pytest.mark.parametrize("levels", [0, 2])
+def test_rmat_s16_deltas_agree(gr, s16w, delta, levels):
+    # levels 0: multi-level queue (8 buckets); 2: near/far
     g, G = s16w
     for src in (gg.max_degree_vertex(g), 4321):
-        d, p = run_sssp(gr, G, src, delta=delta)
+        d, p = run_sssp(gr, G, src, delta=delta, levels=levels)
         check(g, src, d, p)
 
 
@@ -61,29 +64,39 @@ def test_step_stats(gr, s16w):
     cap = 4096
     stats = torch.full((4 * cap,), -7, dtype=torch.int32, device="cuda")
     src = gg.max_degree_vertex(g)
-    for delta in (7, 64):
+    for delta, levels in ((7, 2), (64, 2), (7, 0), (64, 0)):
         stats.fill_(-7)
-        d, p = run_sssp(gr, G, src, delta=delta, level_stats=stats.data_ptr(), max_levels=cap)
+        d, p = run_sssp(gr, G, src, delta=delta, level_stats=stats.data_ptr(), max_levels=cap,
+                        levels=levels)
         check(g, src, d, p)
         steps = gr.gr_last_run_stats(G.handle)["levels"]
         assert 0 < steps < cap
         s = host(stats).reshape(cap, 4)[:steps]
         assert s[0, 0] == 1 and s[0, 1] == 0 and s[0, 2] == 0    # the source alone
         split = s[:, 1] == 1
-        assert (s[split, 0] == 0).all() and (s[split, 2] > 0).all()  # splits drain the far pile
+        assert (s[split, 0] == 0).all()
+        if levels == 2:
+            assert (s[split, 2] > 0).all()    # near/far splits drain the far pile
         assert (s[~split, 0] > 0).all()
         assert (np.diff(s[:, 3]) >= 0).all()
         assert (host(stats).reshape(cap, 4)[steps:] == -7).all()
 
 
 @pytest.mark.parametrize("bulk", [-1, 1, 4096])
-@pytest.mark.parametrize("delta", [0, 7, 1 << 30])
-def test_bulk_and_per_edge_steps_agree(gr, s16w, bulk, delta):
+@pytest.mark.parametrize("delta", [0, 3, 7, 1 << 30])
+@pytest.mark.parametrize("levels", [0, 2])
+def test_bulk_and_per_edge_steps_agree(gr, s16w, bulk, delta, levels):
     # bulk = 1: every relax step runs in bulk; -1: none does; 4096: mixed
     g, G = s16w
     for src in (gg.max_degree_vertex(g), 4321):
-        d, p = run_sssp(gr, G, src, delta=delta, bulk_rows=bulk)
+        d, p = run_sssp(gr, G, src, delta=delta, bulk_rows=bulk, levels=levels)
         check(g, src, d, p)
+
+
+def test_queue_levels_validated(gr, s16w):
+    g, G = s16w
+    with pytest.raises(gr.GrError):
+        run_sssp(gr, G, 0, levels=3)
 
 
 @pytest.mark.parametrize("cap", [1, 7, 38])
@@ -104,10 +117,11 @@ def test_split_thresholds_agree(gr, s16w, big):
 def test_grid_small_wide_weights(gr):
     g = gg.grid_weighted(200, 0.1, seed=3)
     G = gr.Graph.from_csr(g)
-    for delta in (0, 100, 5000):
+    for delta in (0, 30, 100, 5000):
         for bulk in (0, 1):
-            d, p = run_sssp(gr, G, 0, delta=delta, bulk_rows=bulk)
-            check(g, 0, d, p)
+            for levels in (0, 2):
+                d, p = run_sssp(gr, G, 0, delta=delta, bulk_rows=bulk, levels=levels)
+                check(g, 0, d, p)
 
 
 def test_constant_weight_is_scaled_bfs(gr):
@@ -131,8 +145,9 @@ def test_degenerate_graphs(gr):
         for src in {0, g.n - 1}:
             for big in (32, 1024):
                 for bulk in (-1, 1):
-                    d, p = run_sssp(gr, G, src, big_degree=big, bulk_rows=bulk)
-                    check(g, src, d, p)
+                    for delta in (0, 2):
+                        d, p = run_sssp(gr, G, src, big_degree=big, bulk_rows=bulk, delta=delta)
+                        check(g, src, d, p)
         G.close()
 
 
@@ -141,12 +156,14 @@ def test_overflow_detected(gr):
     g.W = np.full(g.m, 2**31, np.uint32)
     G = gr.Graph.from_csr(g)
     for bulk in (-1, 1):
-        run_sssp(gr, G, 0, expect=gr.GR_ERR_OVERFLOW, bulk_rows=bulk)
+        for delta in (0, 1):
+            run_sssp(gr, G, 0, expect=gr.GR_ERR_OVERFLOW, bulk_rows=bulk, delta=delta)
     g.W = np.full(g.m, 2**30, np.uint32)
     G2 = gr.Graph.from_csr(g)
     for bulk in (-1, 1):
-        d, p = run_sssp(gr, G2, 0, bulk_rows=bulk)
-        check(g, 0, d, p)
+        for delta in (0, 1, 2**29):
+            d, p = run_sssp(gr, G2, 0, bulk_rows=bulk, delta=delta)
+            check(g, 0, d, p)
 
 
 def test_sssp_needs_weights(gr):
