@@ -339,13 +339,23 @@ def test_bfs_certificate_rejects_planted_mistakes():
     assert oracle.bfs_certificate(g.R, g.C, src, bad, p) != 0
     bad = d.copy(); bad[v] = -1                       # dropped vertex
     assert oracle.bfs_certificate(g.R, g.C, src, bad, p) != 0
-    badp = p.copy(); badp[v] = int(np.nonzero(d == d[v] - 1)[0][-1])
-    if not np.isin(v, g.C[g.R[badp[v]]:g.R[badp[v] + 1]]):   # parent that is not a neighbour
-        assert oracle.bfs_certificate(g.R, g.C, src, d, badp) != 0
+    # a parent one level up that is not a neighbour of v (one always exists here)
+    up = [int(u) for u in np.nonzero(d == d[v] - 1)[0] if not np.isin(v, g.C[g.R[u]:g.R[u + 1]])]
+    assert up
+    badp = p.copy(); badp[v] = up[0]
+    assert oracle.bfs_certificate(g.R, g.C, src, d, badp) == 11
     badp = p.copy(); badp[v] = v                      # parent at the same level
     assert oracle.bfs_certificate(g.R, g.C, src, d, badp) != 0
     badp = p.copy(); badp[src] = 0 if src else 1
     assert oracle.bfs_certificate(g.R, g.C, src, d, badp) != 0
+
+
+def test_bfs_certificate_without_preds_needs_a_parent_level():
+    # path 0 - 1 - 2 with vertex 2 claimed at depth 1: every edge rule holds, but
+    # 2 has no neighbour at depth 0, which only the no-predecessor check sees
+    g = undirected(3, [(0, 1), (1, 2)])
+    assert oracle.bfs_certificate(g.R, g.C, 0, np.array([0, 1, 2], np.int32)) == 0
+    assert oracle.bfs_certificate(g.R, g.C, 0, np.array([0, 1, 1], np.int32)) == 13
 
 
 def test_sssp_certificate_rejects_planted_mistakes():
