@@ -400,11 +400,20 @@ int32_t orc_bfs_certificate(int32_t n, const int32_t* R, const int32_t* C, int32
       int32_t p = pred[v];
       if (p < 0 || p >= n) return 9;
       if (depth[p] != depth[v] - 1) return 10;
-      int found = 0;                           /* (p, v) must be an edge */
-      for (int64_t e = R[p]; e < R[p + 1]; ++e)
-        if (C[e] == v) { found = 1; break; }
-      if (!found) return 11;
     }
+    /* (pred[v], v) must be an edge: one sweep over the reached rows marks
+       every v whose pred's row lists it (O(m), also on a hub whose row
+       holds most of the graph) */
+    int8_t* ok = (int8_t*)calloc((size_t)(n > 0 ? n : 1), 1);
+    if (!ok) return 12;
+    for (int32_t u = 0; u < n; ++u) {
+      if (depth[u] < 0) continue;
+      for (int64_t e = R[u]; e < R[u + 1]; ++e)
+        if (pred[C[e]] == u) ok[C[e]] = 1;
+    }
+    for (int32_t v = 0; v < n; ++v)
+      if (v != src && depth[v] > 0 && !ok[v]) { free(ok); return 11; }
+    free(ok);
   } else {
     /* without preds, every reached v != src still needs a parent one level up */
     int32_t* has = (int32_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
@@ -440,10 +449,21 @@ int32_t orc_sssp_certificate(int32_t n, const int32_t* R, const int32_t* C, cons
     int32_t p = pred[v];
     if (p < 0 || p >= n) return 6;
     if (dist[p] == ORC_INF32) return 7;
-    int found = 0;                              /* some edge (p, v) must be tight */
-    for (int64_t e = R[p]; e < R[p + 1]; ++e)
-      if (C[e] == v && (uint64_t)dist[p] + W[e] == (uint64_t)dist[v]) { found = 1; break; }
-    if (!found) return 8;
+  }
+  {
+    /* some edge (pred[v], v) must be tight: one O(m) sweep marks them */
+    int8_t* ok = (int8_t*)calloc((size_t)(n > 0 ? n : 1), 1);
+    if (!ok) return 9;
+    for (int32_t u = 0; u < n; ++u) {
+      if (dist[u] == ORC_INF32) continue;
+      for (int64_t e = R[u]; e < R[u + 1]; ++e) {
+        int32_t v = C[e];
+        if (v != src && pred[v] == u && (uint64_t)dist[u] + W[e] == (uint64_t)dist[v]) ok[v] = 1;
+      }
+    }
+    for (int32_t v = 0; v < n; ++v)
+      if (v != src && dist[v] != ORC_INF32 && !ok[v]) { free(ok); return 8; }
+    free(ok);
   }
   /* following pred from any reached vertex must reach src without a cycle */
   int8_t* state = (int8_t*)calloc((size_t)(n > 0 ? n : 1), 1); /* 0 new, 1 on path, 2 ok */

@@ -358,6 +358,31 @@ def test_bfs_certificate_without_preds_needs_a_parent_level():
     assert oracle.bfs_certificate(g.R, g.C, 0, np.array([0, 1, 1], np.int32)) == 13
 
 
+def test_certificates_on_a_hub_are_linear_and_still_strict():
+    # a 400,000-leaf star with a second hub on every third leaf: every leaf's
+    # parent is the hub, so an edge check that walks the parent's row costs
+    # O(deg^2); the certificates must stay O(m) and still see planted parents
+    import time
+    k = 400_000
+    leaves = np.arange(1, k + 1)
+    pairs = np.concatenate([np.stack([np.zeros(k, np.int64), leaves], 1),
+                            np.stack([leaves[::3], np.full(len(leaves[::3]), k + 1)], 1)])
+    g = undirected(k + 2, pairs)
+    W = np.ones(g.m, np.uint32)
+    d, p = oracle.bfs(g.R, g.C, 0)
+    dist, pred, _ = oracle.dijkstra(g.R, g.C, W, 0)
+    t0 = time.perf_counter()
+    assert oracle.bfs_certificate(g.R, g.C, 0, d, p) == 0
+    assert oracle.sssp_certificate(g.R, g.C, W, 0, dist, pred) == 0
+    assert time.perf_counter() - t0 < 5.0
+    # the second hub sits at depth 2 and its row holds leaves 1, 4, 7, ...
+    # only: leaf 2 is one level up but not a neighbour
+    badp = p.copy(); badp[k + 1] = 2
+    assert oracle.bfs_certificate(g.R, g.C, 0, d, badp) == 11
+    badp = pred.copy(); badp[k + 1] = 2
+    assert oracle.sssp_certificate(g.R, g.C, W, 0, dist, badp) == 8
+
+
 def test_sssp_certificate_rejects_planted_mistakes():
     g = gg.rmat(10, 8, seed=42)
     W = gg.weights(g, 1, 64, seed=43)
