@@ -53,7 +53,7 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--workload", choices=["s22", "s16", "grid", "msbfs", "batch", "serve", "ops",
-                                          "push", "bc", "cc", "tc"],
+                                          "push", "bc", "cc", "tc", "static"],
                    default="s22",
                    help="s22 (default, the headline workload) or one of the other configurations")
     p.add_argument("--rates", default="20,2000,5000,10000,20000,50000",
@@ -801,9 +801,12 @@ def ops_algorithmic_bytes(op, f, e, u):
     advance (ordered, no functor): frontier 4 B + row bounds 8 B + per-row output offset
     8 B written and read per row, columns 4 B and outputs 4 B per edge.
     exact-unique and cull filters: 4 B read per input item, 4 B written per output item.
+    multisplit: 4 B read per input item, 8 B key read per item, 4 B written per output item.
     """
     if op == "advance":
         return 4 * f + 8 * f + 16 * f + 8 * e
+    if op == "multisplit":
+        return 12 * e + 4 * u
     return 4 * e + 4 * u
 
 
@@ -918,6 +921,22 @@ def run_other(args):
             if len(got) != U or not mark[got].all() or len(np.unique(got)) != U:
                 raise RuntimeError(f"{name} output is not the {U} distinct neighbours")
             res[name] = (t, ops_algorithmic_bytes("filter", len(Fh), E, U))
+        # multisplit of the advance output into 8 distance buckets (seeded distances)
+        rng = np.random.default_rng(9)
+        dist0 = rng.integers(0, 400, g.n).astype(np.uint64)
+        keys = torch.from_numpy((dist0 << np.uint64(32)).view(np.int64)).cuda()
+        mo = torch.empty(E, dtype=torch.int32, device="cuda")
+        blen = torch.zeros(8, dtype=torch.int64, device="cuda")
+        mst = gr.gr_multisplit_state(key=keys.data_ptr(), base=20, delta=40, buckets=8,
+                                     bucket_len=blen.data_ptr())
+        t = _events_ms(lambda: gr.gr_filter(G.handle, out, E, mo, ul,
+                                            mode=gr.GR_FILTER_MULTISPLIT, state=mst), reps)
+        bk = np.minimum(7, np.maximum(dist0[want].astype(np.int64) - 20, -1) // 40)
+        bk[bk < 0] = 0
+        got_len = blen.cpu().numpy()
+        if not np.array_equal(got_len, np.bincount(bk, minlength=8)) or int(ul.item()) != E:
+            raise RuntimeError("multisplit bucket sizes differ")
+        res["filter_multisplit"] = (t, ops_algorithmic_bytes("multisplit", len(Fh), E, E))
         if G.sync_status() != 0:
             raise RuntimeError("operator status")
         hbm, peak_note = hbm_peak()
@@ -933,7 +952,8 @@ def run_other(args):
               **base, "ms_per_step": tot_ms, "higher_is_better": True,
               "config": {"workload": "rmat_s22_ef16_seed2: advance of the hub's 162,948-row "
                                      "neighbourhood (84.7 M edges), then exact-unique and cull "
-                                     "filters of its output",
+                                     "filters of its output and an 8-bucket multisplit of it "
+                                     "(seeded distances U[0,400), base 20, width 40)",
                          "frontier_rows": len(Fh), "edges": E, "distinct": U,
                          "l2": "inputs larger than L2 (339 MB advance output)"},
               "roofline": {"bound": "hbm", "achieved": adv["gbs"], "peak": hbm, "unit": "GB/s",
@@ -958,6 +978,30 @@ def run_other(args):
               "config": {"workload": "rmat_s22_ef16_seed2: push-only BFS from the highest-degree "
                                      "vertex, then the seeded random sources"},
               "roofline": r["first_source"], **r})
+        return
+    if args.workload == "static":
+        # gr_bfs_static (no allocation, scratch in a static device array) beside gr_bfs on
+        # the largest graph it accepts: R-MAT scale 20 (n = 2^20), edge factor 16
+        g = gg.rmat(20, 16, 1)
+        srcs = [gg.max_degree_vertex(g)] + [int(x) for x in gg.sources(g, 7, seed=1)]
+        G = gr.Graph.from_csr(g)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+        d = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        res = {}
+        for name, fn in (("gr_bfs", lambda s_: gr.gr_bfs(G.handle, s_, d, None)),
+                         ("gr_bfs_static", lambda s_: gr.gr_bfs_static(
+                             g.n, g.m, G.R, G.C, s_, d, None, st, flags=gr.GR_SYMMETRIC))):
+            fn(srcs[0])
+            ts = [statistics.median(_timed(lambda: fn(s_), flush, 3)) for s_ in srcs]
+            res[name] = {"ms_hub": ts[0], "ms_mean": statistics.mean(ts)}
+        ok = G.sync_status() == gr.GR_OK and int(st.item()) == gr.GR_OK
+        G.close()
+        emit({"metric": "ms", "value": res["gr_bfs_static"]["ms_mean"], "unit": "ms", **base,
+              "ms_per_step": res["gr_bfs_static"]["ms_mean"], "higher_is_better": False,
+              "config": {"workload": "rmat_s20_ef16_seed1: BFS from the hub and 7 random "
+                                     "sources, static-scratch entry point vs gr_bfs"},
+              "per_entry": res, "status_ok": ok})
         return
     if args.workload in ("bc", "cc", "tc"):
         # one operator family on R-MAT s22 (the s22 line's bc / cc / tc legs on their own)

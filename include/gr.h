@@ -88,7 +88,8 @@ gr_status gr_graph_create_csr(int32_t n, int64_t m, const int32_t* row_offsets,
                               const int32_t* cols, const uint32_t* weights, uint32_t flags,
                               void* stream, gr_graph** out);
 
-/* Destroy a graph and its default workspace (synchronises the device). */
+/* Destroy a graph and its default workspace (synchronises the device; graphs
+ * are long-lived, workspaces of a server are not: see gr_workspace_destroy_async). */
 gr_status gr_graph_destroy(gr_graph* g);
 
 /* Sizes and flags of a graph; any output pointer may be NULL.  Host call. */
@@ -111,7 +112,25 @@ gr_status gr_graph_footprint(const gr_graph* g, int32_t op, size_t* bytes_per_qu
  * status word).  `ops` is a mask of GR_OP_BFS | GR_OP_SSSP.  Synchronous.
  */
 gr_status gr_workspace_create(const gr_graph* g, int32_t ops, gr_workspace** out);
+/* Waits for the whole device, then releases the workspace. */
 gr_status gr_workspace_destroy(gr_workspace* ws);
+
+/*
+ * Stream-ordered workspaces, for a server whose streams must keep running
+ * while one of them releases memory: the buffers come from the device's
+ * stream-ordered allocator (cudaMallocAsync) and are initialised on `stream`,
+ * so the workspace is ready for work queued on `stream` after the call and
+ * nothing waits for the device.  Work on other streams must be ordered after
+ * `stream` by the caller (events).  gr_workspace_destroy_async releases it
+ * with cudaFreeAsync on `stream`, after the work already queued there; the
+ * caller must also order any other stream that used it before that point.
+ * BC, CC and triangle scratch allocated on such a workspace is released with
+ * cudaFree (which waits for the device).  gr_workspace_destroy_async on a
+ * workspace from gr_workspace_create behaves as gr_workspace_destroy.
+ */
+gr_status gr_workspace_create_async(const gr_graph* g, int32_t ops, void* stream,
+                                    gr_workspace** out);
+gr_status gr_workspace_destroy_async(gr_workspace* ws, void* stream);
 
 /*
  * Wait for `stream`, then read and clear the status word of `ws` (NULL = the
@@ -225,6 +244,23 @@ gr_status gr_advance(const gr_graph* g, const int32_t* in, int64_t in_len,
 #define GR_FILTER_CULL         1 /* inexact: every valid id at least once, no new ids  */
 #define GR_FILTER_UNVISITED    2 /* ignore `in`: all v with depth -1, ascending        */
 #define GR_FILTER_NEAR_FAR     3 /* stable split by dist < threshold (Sec. 5.1.5)      */
+#define GR_FILTER_MULTISPLIT   4 /* stable split into 2..8 distance buckets            */
+
+/*
+ * State of GR_FILTER_MULTISPLIT, the near/far split of Sec. 5.1.5 with more
+ * than two buckets: item v goes to bucket
+ *   b(v) = 0 if dist(v) < base, else min(buckets - 1, (dist(v) - base) / delta),
+ * dist(v) = key[v] >> 32 (the packed SSSP keys of gr_sssp_state).
+ *   buckets in [2, 8]; delta >= 1; bucket_len: device int64[buckets], receives
+ *   the number of items of every bucket.
+ */
+typedef struct gr_multisplit_state {
+  const uint64_t* key;
+  uint32_t base;
+  uint32_t delta;
+  int32_t buckets;
+  int64_t* bucket_len;
+} gr_multisplit_state;
 
 /*
  * One filter step: in (device int32[in_len]) -> out (+ far for NEAR_FAR).
@@ -239,6 +275,10 @@ gr_status gr_advance(const gr_graph* g, const int32_t* in, int64_t in_len,
  *   NEAR_FAR: state = gr_sssp_state*; near items (dist < threshold) go to
  *     out, the rest to far, both in input order.  far/far_cap/far_len are
  *     required for this mode only.
+ *   MULTISPLIT: state = gr_multisplit_state*; out = the items of bucket 0 in
+ *     input order, then bucket 1, ...; bucket_len[j] = the items of bucket j;
+ *     out_len = their total.  Uses a temporary from the stream-ordered
+ *     allocator (8 bytes per bucket and 4096 items).
  * Lengths/capacities behave as in gr_advance.  Scratch comes from the
  * graph's default workspace, so concurrent filters on one graph must use
  * distinct streams serialised by the caller.
@@ -268,7 +308,10 @@ typedef struct gr_bfs_opts {
   gr_workspace* ws;      /* NULL = the graph's default workspace              */
   int32_t* level_stats;  /* optional device int32[4*max_levels]: per level
                             (frontier size, 1 if pull, sum of the frontier's
-                            degrees m_f, start time in ns after level 0)   */
+                            degrees m_f, start time in ns after the kernel
+                            started, so level 0's start shows the
+                            initialisation); one more row (frontier 0)
+                            records when the level loop ended            */
   int32_t max_levels;    /* capacity of level_stats in levels                 */
   int32_t max_blocks;    /* upper bound on the persistent grid's CTAs; 0 = none.
                             A query on a high-diameter graph (small frontiers,
@@ -308,7 +351,9 @@ typedef struct gr_sssp_opts {
   gr_workspace* ws;      /* NULL = the graph's default workspace              */
   int32_t* level_stats;  /* optional device int32[4*max_levels]: per step
                             (near rows, 1 if a SPLIT step, far-pile length,
-                            start time in ns after the first step)          */
+                            start time in ns after the kernel started); one
+                            more row (0, 0, 0, time) records when the step
+                            loop ended, before the distances are unpacked  */
   int32_t max_levels;    /* capacity of level_stats in steps                  */
   int32_t bulk_rows;     /* near frontiers of at least this many rows (a row
                             of 32 or more edges counts as 4, an edge chunk of
@@ -543,7 +588,7 @@ gr_status gr_triangle_count(const gr_graph* g, int64_t* total, int64_t* per_vert
  * synchronisation cudaMalloc may cause, or a host runtime that owns all
  * device memory.  It runs the same persistent BFS as gr_bfs, but takes the
  * CSR directly (no gr_graph handle, which would allocate) and keeps every
- * scratch buffer in one statically sized __device__ array of about 11 MB
+ * scratch buffer in one statically sized __device__ array of about 13 MB
  * that each GPU loading this library reserves until the process exits.  The
  * call allocates nothing.
  *

@@ -36,6 +36,7 @@ GR_OP_BFS, GR_OP_SSSP = 1, 2
 GR_V2V, GR_V2E, GR_PUSH, GR_PULL, GR_ORDERED, GR_UNORDERED, GR_IDEMPOTENT = 0, 1, 0, 2, 0, 4, 8
 GR_FN_NONE, GR_FN_BFS_VISIT, GR_FN_SSSP_RELAX = 0, 1, 2
 GR_FILTER_EXACT_UNIQUE, GR_FILTER_CULL, GR_FILTER_UNVISITED, GR_FILTER_NEAR_FAR = 0, 1, 2, 3
+GR_FILTER_MULTISPLIT = 4
 GR_DIR_AUTO, GR_DIR_PUSH, GR_DIR_PULL = 0, 1, 2
 
 
@@ -58,6 +59,11 @@ class gr_bfs_state(ctypes.Structure):
 
 class gr_sssp_state(ctypes.Structure):
     _fields_ = [("key", c_vp), ("threshold", c_u32)]
+
+
+class gr_multisplit_state(ctypes.Structure):
+    _fields_ = [("key", c_vp), ("base", c_u32), ("delta", c_u32), ("buckets", c_i32),
+                ("bucket_len", c_vp)]
 
 
 class gr_msbfs_opts(ctypes.Structure):
@@ -109,6 +115,8 @@ _SIGNATURES = {
     "gr_graph_footprint": ([c_vp, c_i32, ctypes.POINTER(ctypes.c_size_t)], c_i32),
     "gr_workspace_create": ([c_vp, c_i32, ctypes.POINTER(c_vp)], c_i32),
     "gr_workspace_destroy": ([c_vp], c_i32),
+    "gr_workspace_create_async": ([c_vp, c_i32, c_vp, ctypes.POINTER(c_vp)], c_i32),
+    "gr_workspace_destroy_async": ([c_vp, c_vp], c_i32),
     "gr_sync_status": ([c_vp, c_vp, c_vp], c_i32),
     "gr_last_run_stats": ([c_vp, c_vp, ctypes.POINTER(gr_run_stats), c_vp], c_i32),
     "gr_advance": ([c_vp, c_vp, c_i64, c_vp, c_i32, c_i32, c_vp, c_vp, c_i64, c_vp, c_vp], c_i32),
@@ -258,6 +266,20 @@ def gr_workspace_create(g, ops=GR_OP_BFS | GR_OP_SSSP):
 
 def gr_workspace_destroy(ws):
     _check(load().gr_workspace_destroy(c_vp(ws)), "gr_workspace_destroy")
+
+
+def gr_workspace_create_async(g, ops=GR_OP_BFS | GR_OP_SSSP, stream=None):
+    """Stream-ordered workspace: allocated and initialised on `stream`, no device wait."""
+    h = c_vp()
+    _check(load().gr_workspace_create_async(c_vp(g), ops, _stream(stream), ctypes.byref(h)),
+           "gr_workspace_create_async")
+    return h.value
+
+
+def gr_workspace_destroy_async(ws, stream=None):
+    """Release a stream-ordered workspace after the work queued on `stream`."""
+    _check(load().gr_workspace_destroy_async(c_vp(ws), _stream(stream)),
+           "gr_workspace_destroy_async")
 
 
 def gr_sync_status(g, ws=None, stream=None) -> int:

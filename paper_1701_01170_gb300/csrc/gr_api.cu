@@ -9,6 +9,7 @@
 #include <mutex>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "gr_internal.cuh"
 
@@ -175,20 +176,55 @@ static size_t ws_bytes(const gr_graph* g, int32_t ops) {
   return b;
 }
 
-static void ws_free(gr_workspace* ws) {
+// Pinned host words for gr_sync_status, handed out from blocks that live until
+// the process exits, so that creating or destroying a workspace never calls
+// cudaMallocHost / cudaFreeHost (the latter waits for the whole device).
+namespace {
+std::mutex g_slot_mu;
+std::vector<int*> g_slot_free;
+constexpr int kSlotBlock = 1024;
+}  // namespace
+
+static int* status_slot_take() {
+  std::lock_guard<std::mutex> lock(g_slot_mu);
+  if (g_slot_free.empty()) {
+    int* block = nullptr;
+    if (cudaMallocHost((void**)&block, kSlotBlock * sizeof(int)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return nullptr;
+    }
+    for (int i = kSlotBlock - 1; i >= 0; --i) g_slot_free.push_back(block + i);
+  }
+  int* p = g_slot_free.back();
+  g_slot_free.pop_back();
+  return p;
+}
+
+static void status_slot_give(int* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lock(g_slot_mu);
+  g_slot_free.push_back(p);
+}
+
+// Releases a workspace: device buffers with cudaFree, or, for a stream-ordered
+// workspace, with cudaFreeAsync on `s` (after the work already queued there).
+static void ws_free(gr_workspace* ws, cudaStream_t s = nullptr) {
   if (!ws) return;
+  auto release = [&](void* p) {
+    if (!p) return;
+    if (ws->stream_ordered) cudaFreeAsync(p, s);
+    else cudaFree(p);
+  };
   void* ptrs[] = {ws->ctl, ws->status, ws->q[0], ws->q[1], ws->qm[0], ws->qm[1],
                   ws->ulist[0], ws->ulist[1],
                   ws->chunks[0], ws->chunks[1],
                   ws->visited, ws->front[0], ws->front[1], ws->front[2], ws->key,
                   ws->far[0], ws->far[1], ws->stamp_near, ws->stamp_far, ws->first_idx,
                   ws->claim, ws->block_sums, ws->tags, ws->item_off, ws->dev_len};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
-  for (int j = 0; j < GR_RING_K; ++j)
-    if (ws->ring[j]) cudaFree(ws->ring[j]);
-  if (ws->stamp_ring) cudaFree(ws->stamp_ring);
-  if (ws->h_status) cudaFreeHost(ws->h_status);
+  for (void* p : ptrs) release(p);
+  for (int j = 0; j < GR_RING_K; ++j) release(ws->ring[j]);
+  release(ws->stamp_ring);
+  status_slot_give(ws->h_status);
   gr_bc_free(ws->bc);
   gr_cc_free(ws->cc);
   gr_tc_free(ws->tc);
@@ -201,20 +237,26 @@ __global__ void gr_fill_i32(int32_t* p, int64_t len, int32_t v) {
     p[i] = v;
 }
 
-static gr_status ws_create(const gr_graph* g, int32_t ops, gr_workspace** out) {
+// stream_ordered: allocate with cudaMallocAsync and initialise on `s`, without
+// waiting for the device (the workspace is then ready in the order of `s`).
+static gr_status ws_create(const gr_graph* g, int32_t ops, gr_workspace** out,
+                           bool stream_ordered = false, cudaStream_t s = nullptr) {
   gr_workspace* ws = new (std::nothrow) gr_workspace();
   if (!ws) return GR_ERR_OOM;
   ws->g = g;
   ws->ops = ops;
+  ws->stream_ordered = stream_ordered;
   size_t n = (size_t)g->n + 1, bw = bitmap_words(g->n);
   ws->chunk_cap = chunk_capacity(g, 32);
-#define ALLOC(ptr, bytes)                                   \
-  do {                                                      \
-    if (cudaMalloc((void**)&(ptr), (bytes)) != cudaSuccess) { \
-      (void)cudaGetLastError();                             \
-      ws_free(ws);                                          \
-      return GR_ERR_OOM;                                    \
-    }                                                       \
+#define ALLOC(ptr, bytes)                                                      \
+  do {                                                                         \
+    const cudaError_t e_ = stream_ordered ? cudaMallocAsync((void**)&(ptr), (bytes), s) \
+                                          : cudaMalloc((void**)&(ptr), (bytes));        \
+    if (e_ != cudaSuccess) {                                                   \
+      (void)cudaGetLastError();                                                \
+      ws_free(ws, s);                                                          \
+      return GR_ERR_OOM;                                                       \
+    }                                                                          \
   } while (0)
   ALLOC(ws->ctl, sizeof(GrCtl));
   ALLOC(ws->status, sizeof(int));
@@ -244,21 +286,22 @@ static gr_status ws_create(const gr_graph* g, int32_t ops, gr_workspace** out) {
     ALLOC(ws->stamp_ring, n * sizeof(uint32_t));
   }
 #undef ALLOC
-  if (cudaMallocHost((void**)&ws->h_status, sizeof(int)) != cudaSuccess) {
-    (void)cudaGetLastError();
-    ws_free(ws);
+  ws->h_status = status_slot_take();
+  if (!ws->h_status) {
+    ws_free(ws, s);
     return GR_ERR_OOM;
   }
-  bool ok = cudaMemset(ws->ctl, 0, sizeof(GrCtl)) == cudaSuccess &&
-            cudaMemset(ws->status, 0, sizeof(int)) == cudaSuccess &&
-            cudaMemset(ws->claim, 0, bw * sizeof(uint32_t)) == cudaSuccess;
+  bool ok = cudaMemsetAsync(ws->ctl, 0, sizeof(GrCtl), s) == cudaSuccess &&
+            cudaMemsetAsync(ws->status, 0, sizeof(int), s) == cudaSuccess &&
+            cudaMemsetAsync(ws->claim, 0, bw * sizeof(uint32_t), s) == cudaSuccess;
   if (ok) {
-    gr_fill_i32<<<256, 256>>>(ws->first_idx, (int64_t)n, INT32_MAX);
-    ok = cudaGetLastError() == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
+    gr_fill_i32<<<256, 256, 0, s>>>(ws->first_idx, (int64_t)n, INT32_MAX);
+    ok = cudaGetLastError() == cudaSuccess &&
+         (stream_ordered || cudaDeviceSynchronize() == cudaSuccess);
   }
   if (!ok) {
     (void)cudaGetLastError();
-    ws_free(ws);
+    ws_free(ws, s);
     return GR_ERR_CUDA;
   }
   *out = ws;
@@ -276,6 +319,21 @@ extern "C" gr_status gr_workspace_destroy(gr_workspace* ws) {
   if (!ws) return GR_ERR_INVALID_ARG;
   cudaDeviceSynchronize();
   ws_free(ws);
+  return GR_OK;
+}
+
+extern "C" gr_status gr_workspace_create_async(const gr_graph* g, int32_t ops, void* stream,
+                                               gr_workspace** out) {
+  if (!g || !out || (ops & ~(GR_OP_BFS | GR_OP_SSSP))) return GR_ERR_INVALID_ARG;
+  if ((ops & GR_OP_SSSP) && !g->W && g->m > 0) return GR_ERR_UNSUPPORTED;
+  *out = nullptr;
+  return ws_create(g, ops, out, true, (cudaStream_t)stream);
+}
+
+extern "C" gr_status gr_workspace_destroy_async(gr_workspace* ws, void* stream) {
+  if (!ws) return GR_ERR_INVALID_ARG;
+  if (!ws->stream_ordered) return gr_workspace_destroy(ws);
+  ws_free(ws, (cudaStream_t)stream);
   return GR_OK;
 }
 

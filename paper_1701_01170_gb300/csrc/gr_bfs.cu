@@ -166,7 +166,9 @@ namespace {
 
 constexpr int64_t kStaticMaxVertices = GR_STATIC_MAX_VERTICES;
 constexpr int64_t kStaticMaxEdges = GR_STATIC_MAX_EDGES;
-constexpr int kStaticBig = GR_DEFAULT_BIG_DEGREE;  // no medium class here: 32-row batches
+// rows of at least 256 edges (the BFS default) are split into chunks; there is
+// no medium-row class here, so a 32-row batch holds at most 32 x 255 edges
+constexpr int kStaticBig = GR_DEFAULT_BFS_BIG;
 // chunks of one frontier: at most m / chunk + m / kStaticBig + 1 entries
 constexpr int64_t kStaticChunkCap =
     kStaticMaxEdges / GR_CHUNK_EDGES + kStaticMaxEdges / kStaticBig + 2;
@@ -184,7 +186,7 @@ constexpr size_t kOffCh1 = kOffCh0 + kChunkBytes;
 constexpr size_t kBitmapBytes = round256((size_t)kStaticWords * sizeof(uint32_t));
 constexpr size_t kOffVisited = kOffCh1 + kChunkBytes;
 constexpr size_t kOffFront = kOffVisited + kBitmapBytes;
-constexpr size_t kStaticBytes = kOffFront + 3 * kBitmapBytes;  // about 11 MB
+constexpr size_t kStaticBytes = kOffFront + 3 * kBitmapBytes;  // about 13.1 MB
 
 static __device__ __align__(256) unsigned char g_bfs_static_scratch[kStaticBytes];
 

@@ -174,6 +174,7 @@ struct gr_workspace {
   GrBcScratch* bc;      // allocated by the first gr_bc call on this workspace
   GrCcScratch* cc;      // allocated by the first gr_cc call on this workspace
   GrTcScratch* tc;      // allocated by the first intersection / triangle call
+  bool stream_ordered;  // buffers from cudaMallocAsync, released with cudaFreeAsync
 };
 
 // ---------------------------------------------------------------------------

@@ -148,6 +148,7 @@ __device__ __forceinline__ int64_t search_item(const long long* item_off,
 enum { FN_NONE_ORDERED = 0, FN_NONE_EDGES = 1, FN_BFS = 2, FN_BFS_IDEM = 3, FN_RELAX = 4 };
 
 struct ExpandArgs {
+  int32_t n;
   const int32_t* R;
   const int32_t* C;
   const uint32_t* W;
@@ -168,32 +169,69 @@ struct ExpandArgs {
   unsigned long long* key;
 };
 
-// Output-balanced expansion: warp w owns output positions [32w, 32w + 32).
+// Output-balanced expansion over output tiles: a CTA owns GR_ADV_TILE
+// consecutive output positions at a time.  One thread finds the tile's first
+// and last input items (two binary searches over the scanned offsets); the
+// items in between — their offsets, vertex ids and row starts — are staged in
+// shared memory, and every output position then finds its item with a search
+// in shared memory.  A warp's 32 outputs are consecutive positions, so the
+// column loads and the output stores are coalesced.  A tile that spans more
+// items than the stage holds (a run of empty rows) searches global memory.
+#define GR_ADV_PER_THREAD 8
+#define GR_ADV_TILE (T * GR_ADV_PER_THREAD)
 template <int FN>
 __global__ void adv_expand(ExpandArgs a) {
+  __shared__ long long s_off[GR_ADV_TILE + 1];
+  __shared__ int s_beg[GR_ADV_TILE + 1];
+  __shared__ int s_u[GR_ADV_TILE + 1];
+  __shared__ long long s_i0, s_ni;
   int64_t len = eff_len(a.len_dev, a.len_host);
   long long total = *a.total;
   int lane = threadIdx.x & 31;
-  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   long long limit = total;
   if (FN == FN_NONE_ORDERED || FN == FN_NONE_EDGES) limit = total < a.cap ? total : a.cap;
-  for (long long p0 = warp * 32; p0 < limit; p0 += nwarps * 32) {
-    // narrow the search range with the warp's first and last positions
-    long long plast = min(p0 + 31, limit - 1);
-    int64_t lo = 0, hi = 0;
-    if (lane == 0) lo = search_item(a.item_off, a.block_sums, 0, len - 1, p0);
-    if (lane == 31) hi = search_item(a.item_off, a.block_sums, 0, len - 1, plast);
-    lo = __shfl_sync(GR_FULL_MASK, lo, 0);
-    hi = __shfl_sync(GR_FULL_MASK, hi, 31);
-    long long p = p0 + lane;
-    bool active = p < limit;
+  for (long long t0 = (long long)blockIdx.x * GR_ADV_TILE; t0 < limit;
+       t0 += (long long)gridDim.x * GR_ADV_TILE) {
+    const long long tend = min(t0 + (long long)GR_ADV_TILE, limit);
+    if (threadIdx.x == 0) {
+      const int64_t i0 = search_item(a.item_off, a.block_sums, 0, len - 1, t0);
+      const int64_t i1 = search_item(a.item_off, a.block_sums, i0, len - 1, tend - 1);
+      s_i0 = i0;
+      s_ni = i1 - i0 + 1;
+    }
+    __syncthreads();
+    const int64_t i0 = s_i0, ni = s_ni;
+    const bool staged = ni <= GR_ADV_TILE + 1;
+    if (staged) {
+      for (int j = threadIdx.x; j < ni; j += T) {
+        const int64_t i = i0 + j;
+        const int32_t u = a.in[i];
+        s_off[j] = item_offset(a.item_off, a.block_sums, i);
+        s_u[j] = u;
+        s_beg[j] = u >= 0 && u < a.n ? a.R[u] : 0;  // invalid items have no outputs
+      }
+    }
+    __syncthreads();
+    for (int k = 0; k < GR_ADV_PER_THREAD; ++k) {
+    const long long p = t0 + (long long)k * T + threadIdx.x;
+    bool active = p < tend;
     int32_t v = 0, u = 0;
     int e = 0;
     if (active) {
-      int64_t i = search_item(a.item_off, a.block_sums, lo, hi, p);
-      u = a.in[i];
-      e = a.R[u] + (int)(p - item_offset(a.item_off, a.block_sums, i));
+      if (staged) {
+        int lo = 0, hi = (int)ni - 1;  // largest j with s_off[j] <= p
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_off[mid] <= p) lo = mid;
+          else hi = mid - 1;
+        }
+        u = s_u[lo];
+        e = s_beg[lo] + (int)(p - s_off[lo]);
+      } else {
+        const int64_t i = search_item(a.item_off, a.block_sums, i0, i0 + ni - 1, p);
+        u = a.in[i];
+        e = a.R[u] + (int)(p - item_offset(a.item_off, a.block_sums, i));
+      }
       v = __ldg(a.C + e);
     }
     if (FN == FN_NONE_ORDERED) {
@@ -233,6 +271,8 @@ __global__ void adv_expand(ExpandArgs a) {
       }
       warp_append64(a.out, a.out_len, a.cap, improved, v, lane, a.status);
     }
+    }
+    __syncthreads();  // the next tile overwrites the stage
   }
 }
 
@@ -483,6 +523,7 @@ extern "C" gr_status gr_advance(const gr_graph* g, const int32_t* in, int64_t in
                                                  ws->block_sums, ws->status);
   scan_block_sums<<<1, 1024, 0, s>>>(ws->block_sums, tiles, 0, ws->dev_len);
   ExpandArgs a = {};
+  a.n = g->n;
   a.R = g->R; a.C = g->C; a.W = g->W; a.in = in; a.len_host = in_len; a.len_dev = in_len_dev;
   a.item_off = item_off; a.block_sums = ws->block_sums; a.total = ws->dev_len; a.out = out;
   a.cap = out_cap; a.out_len = olen; a.status = ws->status;
@@ -510,12 +551,104 @@ extern "C" gr_status gr_advance(const gr_graph* g, const int32_t* in, int64_t in
   return launched ? GR_OK : GR_ERR_CUDA;
 }
 
+// ---------------------------------------------------------------------------
+// multisplit: a stable K-way partition by distance bucket (the near/far split
+// of Sec. 5.1.5 with more than two buckets)
+
+struct MsplitArgs {
+  int32_t n;
+  const int32_t* in;
+  int64_t len_host;
+  const int64_t* len_dev;
+  const unsigned long long* key;
+  uint32_t base, delta;
+  int K;
+  long long* counts;  // K x tiles, bucket-major (scanned in place between the passes)
+  int64_t tiles;
+  int32_t* out;
+  int64_t cap;
+  int* status;
+};
+
+// Bucket of item v: -1 when v is not in [0, n), else min(K - 1, (d - base) / delta)
+// for d = dist(v) >= base, and 0 below base.
+__device__ __forceinline__ int msplit_bucket(const MsplitArgs& a, int32_t v) {
+  if (v < 0 || v >= a.n) return -1;
+  const unsigned d = (unsigned)(a.key[v] >> 32);
+  const unsigned long long b = d < a.base ? 0ull : (unsigned long long)(d - a.base) / a.delta;
+  return b >= (unsigned long long)(a.K - 1) ? a.K - 1 : (int)b;
+}
+
+__global__ void msplit_count(MsplitArgs a) {
+  __shared__ int s_cnt[GR_RING_K];
+  if (threadIdx.x < GR_RING_K) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t len = eff_len(a.len_dev, a.len_host);
+  const int64_t base = (int64_t)blockIdx.x * TILE + (int64_t)threadIdx.x * ITEMS;
+  for (int k = 0; k < ITEMS && base + k < len; ++k) {
+    const int b = msplit_bucket(a, a.in[base + k]);
+    if (b >= 0) atomicAdd(&s_cnt[b], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < a.K) a.counts[(int64_t)threadIdx.x * a.tiles + blockIdx.x] = s_cnt[threadIdx.x];
+}
+
+// Each thread owns ITEMS consecutive items of the tile, so per-bucket block scans of
+// the threads' counts give every item its place after the earlier items of its bucket.
+__global__ void msplit_scatter(MsplitArgs a) {
+  const int64_t len = eff_len(a.len_dev, a.len_host);
+  const int64_t base = (int64_t)blockIdx.x * TILE + (int64_t)threadIdx.x * ITEMS;
+  signed char bk[ITEMS];
+  int c[GR_RING_K];
+#pragma unroll
+  for (int j = 0; j < GR_RING_K; ++j) c[j] = 0;
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    bk[k] = base + k < len ? (signed char)msplit_bucket(a, a.in[base + k]) : (signed char)-1;
+#pragma unroll
+    for (int j = 0; j < GR_RING_K; ++j) c[j] += bk[k] == j;
+  }
+  long long pos[GR_RING_K];
+#pragma unroll
+  for (int j = 0; j < GR_RING_K; ++j) {
+    long long tot;
+    const long long pre = block_excl_scan<T>(j < a.K ? c[j] : 0, &tot);
+    pos[j] = j < a.K ? a.counts[(int64_t)j * a.tiles + blockIdx.x] + pre : 0;
+  }
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    const int b = bk[k];
+    if (b < 0) continue;
+    long long at = 0;
+#pragma unroll
+    for (int j = 0; j < GR_RING_K; ++j)
+      if (j == b) at = pos[j]++;
+    if (at < a.cap) a.out[at] = a.in[base + k];
+    else gr_set_status(a.status, GR_ERR_CAPACITY);
+  }
+}
+
+// bucket_len[j] from the scanned counts; the total goes to out_len.
+__global__ void msplit_lens(const long long* counts, int64_t tiles, int K, const long long* total,
+                            int64_t* bucket_len, unsigned long long* out_len, int64_t cap,
+                            int* status) {
+  const int j = threadIdx.x;
+  if (j < K) {
+    const long long next = j + 1 < K ? counts[(int64_t)(j + 1) * tiles] : *total;
+    bucket_len[j] = next - counts[(int64_t)j * tiles];
+  }
+  if (j == 0) {
+    *out_len = (unsigned long long)*total;
+    if (*total > cap) gr_set_status(status, GR_ERR_CAPACITY);
+  }
+}
+
 extern "C" gr_status gr_filter(const gr_graph* g, const int32_t* in, int64_t in_len,
                                const int64_t* in_len_dev, int32_t mode, const void* state,
                                int32_t* out, int64_t out_cap, int64_t* out_len, int32_t* far,
                                int64_t far_cap, int64_t* far_len, void* stream) {
   if (!g || in_len < 0 || in_len >= INT32_MAX || out_cap < 0 || !out_len ||
-      (out_cap > 0 && !out) || mode < GR_FILTER_EXACT_UNIQUE || mode > GR_FILTER_NEAR_FAR)
+      (out_cap > 0 && !out) || mode < GR_FILTER_EXACT_UNIQUE || mode > GR_FILTER_MULTISPLIT)
     return GR_ERR_INVALID_ARG;
   if (mode != GR_FILTER_UNVISITED && in_len > 0 && !in) return GR_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -556,6 +689,39 @@ extern "C" gr_status gr_filter(const gr_graph* g, const int32_t* in, int64_t in_
     scan_block_sums<<<1, 1024, 0, s>>>(ws->block_sums, tiles, 1, ws->dev_len);
     compact_scatter<CL_NEAR_FAR><<<(unsigned)tiles, T, 0, s>>>(a);
     GR_LAUNCH_CHECK();
+    return GR_OK;
+  }
+  if (mode == GR_FILTER_MULTISPLIT) {
+    const gr_multisplit_state* st = (const gr_multisplit_state*)state;
+    if (!st || !st->key || !st->bucket_len || st->buckets < 2 || st->buckets > GR_RING_K ||
+        st->delta == 0)
+      return GR_ERR_INVALID_ARG;
+    if (in_len == 0) {
+      if (cudaMemsetAsync(out_len, 0, 8, s) ||
+          cudaMemsetAsync(st->bucket_len, 0, (size_t)st->buckets * 8, s))
+        return GR_ERR_CUDA;
+      return GR_OK;
+    }
+    MsplitArgs m = {};
+    m.n = g->n; m.in = in; m.len_host = in_len; m.len_dev = in_len_dev;
+    m.key = (const unsigned long long*)st->key; m.base = st->base; m.delta = st->delta;
+    m.K = st->buckets; m.tiles = tiles_for(in_len); m.out = out; m.cap = out_cap;
+    m.status = ws->status;
+    const size_t cbytes = (size_t)m.K * (size_t)m.tiles * sizeof(long long);
+    if (cudaMallocAsync((void**)&m.counts, cbytes, s) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return GR_ERR_OOM;
+    }
+    msplit_count<<<(unsigned)m.tiles, T, 0, s>>>(m);
+    scan_block_sums<<<1, 1024, 0, s>>>(m.counts, (int64_t)m.K * m.tiles, 0, ws->dev_len);
+    msplit_scatter<<<(unsigned)m.tiles, T, 0, s>>>(m);
+    msplit_lens<<<1, 32, 0, s>>>(m.counts, m.tiles, m.K, ws->dev_len, st->bucket_len, olen,
+                                 out_cap, ws->status);
+    const bool launched = cudaGetLastError() == cudaSuccess;
+    if (cudaFreeAsync(m.counts, s) != cudaSuccess || !launched) {
+      (void)cudaGetLastError();
+      return GR_ERR_CUDA;
+    }
     return GR_OK;
   }
   if (in_len == 0)

@@ -78,6 +78,7 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
   const int wpc = (int)(blockDim.x >> 5);
   const int swarp = (int)((gwarp % wpc) * (nwarps / wpc) + gwarp / wpc);
   GrCtl* ctl = a.ctl;
+  const unsigned long long t_entry = gr_globaltimer();  // time base of level_stats
 
   // ---- Set_Problem_Data (Alg. 1): labels infinite, preds -1, root 0 -----
   for (int64_t v = gtid; v < a.n; v += gthreads) {
@@ -161,9 +162,9 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
         a.level_stats[4 * it] = nq + nqm + s_nbig;
         a.level_stats[4 * it + 1] = nrows == 0;
         a.level_stats[4 * it + 2] = flen;
-        // start of this step in ns after the first step started
+        // start of this step in ns after the kernel started
         a.level_stats[4 * it + 3] =
-            (int)min(gr_globaltimer() - (deadline - GR_TIME_LIMIT_NS), (unsigned long long)INT_MAX);
+            (int)min(gr_globaltimer() - t_entry, (unsigned long long)INT_MAX);
       }
       ctl->qlen[s2] = 0;
       ctl->qmlen[s2] = 0;
@@ -552,6 +553,14 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
     far_stage.copy_out(a.far[fe_out & 1], a.n);
     bstage.copy_out(chn, a.chunk_cap, a.status);
     if (!sc.sync()) return;
+  }
+  // one more row: the step loop's end (no near rows, no split)
+  if (gtid == 0 && a.level_stats && it < a.max_levels) {
+    a.level_stats[4 * it] = 0;
+    a.level_stats[4 * it + 1] = 0;
+    a.level_stats[4 * it + 2] = 0;
+    a.level_stats[4 * it + 3] =
+        (int)min(gr_globaltimer() - t_entry, (unsigned long long)INT_MAX);
   }
   // ---- overflow check: with every unrepresentable candidate dropped, a
   // vertex keeps an infinite label while a reached neighbour exists only if

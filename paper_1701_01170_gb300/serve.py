@@ -38,6 +38,7 @@ class Request:
     t_done: float | None = None
     result: object = None          # host numpy array (depth or dist)
     status: int = 0
+    lane: int = -1                 # the lane that ran it
 
 
 @dataclass
@@ -178,6 +179,7 @@ class GpuBackend:
                                  gr_graph_footprint(G.handle, GR_OP_SSSP))
                           for name, G in graphs.items()}
         self.graph_blocks: dict[str, int] = {}   # name -> CTA cap of its queries (0: none)
+        self.evicted = 0                          # workspaces released by evictions
 
     def calibrate(self, names, srcs: dict, slack: float = 1.5):
         """Cap the CTAs of a graph's queries at SMs / lanes when that costs a query at
@@ -229,18 +231,22 @@ class GpuBackend:
         torch.cuda.synchronize()
 
     def evict(self, lane: int, keys):
-        from . import gr_workspace_destroy
+        """Release a lane's workspaces in the order of the lane's stream: the other lanes'
+        streams keep running (nothing waits for the whole device)."""
+        from . import gr_workspace_destroy_async
         for key in keys:
             ws = self.ws[lane].pop(key, None)
             if ws:
-                gr_workspace_destroy(ws)
+                gr_workspace_destroy_async(ws, self.streams[lane])
+                self.evicted += 1
 
     def _workspace(self, lane, graph, op):
-        from . import GR_OP_BFS, GR_OP_SSSP, gr_workspace_create
+        from . import GR_OP_BFS, GR_OP_SSSP, gr_workspace_create_async
         key = (graph, op)
         if key not in self.ws[lane]:
-            self.ws[lane][key] = gr_workspace_create(self.graphs[graph].handle,
-                                                     GR_OP_BFS if op == OP_BFS else GR_OP_SSSP)
+            self.ws[lane][key] = gr_workspace_create_async(
+                self.graphs[graph].handle, GR_OP_BFS if op == OP_BFS else GR_OP_SSSP,
+                self.streams[lane])
         return self.ws[lane][key]
 
     def run(self, lane: int, unit: Unit, t0: float):
@@ -252,6 +258,7 @@ class GpuBackend:
         now = time.perf_counter() - t0
         for r in unit.requests:
             r.t_start = now
+            r.lane = lane
         with torch.cuda.stream(s):
             if unit.multi:
                 k = len(unit.requests)
@@ -288,6 +295,7 @@ class GpuBackend:
     def close(self):
         for lane in range(len(self.ws)):
             self.evict(lane, list(self.ws[lane].keys()))
+        self.torch.cuda.synchronize()
 
 
 def serve_trace(backend, trace: list[Request], lanes: int, budget: int, multi_names=(),

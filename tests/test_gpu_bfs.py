@@ -83,6 +83,8 @@ def test_level_stats(gr, s16):
     for L in range(levels):                              # m_f per level = sum of degrees
         assert s[L, 2] == min(int(deg[d == L].sum()), 2**31 - 1)
     assert s[0, 3] >= 0 and (np.diff(s[:levels, 3]) >= 0).all()   # level start times
+    end = s[levels]                                       # the loop's end row
+    assert end[0] == 0 and end[3] >= s[levels - 1, 3]
 
 
 def test_small_and_degenerate_graphs(gr):

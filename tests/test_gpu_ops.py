@@ -229,6 +229,46 @@ def test_filter_near_far(gr, rmat14, k):
     assert np.array_equal(host(far)[:int(fl.item())], far_w)
 
 
+@pytest.mark.parametrize("k", [1, 4097, 40000])
+@pytest.mark.parametrize("buckets,base,delta", [(2, 0, 100), (8, 30, 17), (5, 250, 1),
+                                                (8, 0, 1 << 31)])
+def test_filter_multisplit(gr, rmat14, k, buckets, base, delta):
+    import torch
+    g, G = rmat14
+    rng = np.random.default_rng(k + buckets)
+    dist0 = rng.integers(0, 400, g.n).astype(np.uint32)
+    dist0[::13] = oracle.INF32
+    keys = dev(pack_keys(dist0, np.full(g.n, -1)))
+    items = rng.integers(-2, g.n + 2, k).astype(np.int32)
+    want, want_len = oracle.multisplit(g.n, items, dist0, base, delta, buckets)
+    blen = torch.full((buckets,), -7, dtype=torch.int64, device="cuda")
+    st = gr.gr_multisplit_state(key=keys.data_ptr(), base=base, delta=delta, buckets=buckets,
+                                bucket_len=blen.data_ptr())
+    out, ol = empty_i32(k), len_tensor()
+    gr.gr_filter(G.handle, dev(items), k, out, ol, mode=gr.GR_FILTER_MULTISPLIT, state=st)
+    assert G.sync_status() == 0
+    assert int(ol.item()) == len(want)
+    assert np.array_equal(host(out)[:len(want)], want)
+    assert np.array_equal(host(blen), want_len)
+    if buckets == 2 and base == 0:               # two buckets: the near/far split
+        near, far = oracle.filter_near_far(g.n, items, dist0, delta)
+        assert np.array_equal(want, np.concatenate([near, far]))
+
+
+def test_filter_multisplit_rejects_bad_states(gr, rmat14):
+    import torch
+    g, G = rmat14
+    keys = torch.zeros(g.n, dtype=torch.int64, device="cuda")
+    blen = torch.zeros(9, dtype=torch.int64, device="cuda")
+    out, ol = empty_i32(4), len_tensor()
+    items = dev(np.arange(4, dtype=np.int32))
+    for buckets, delta in ((1, 5), (9, 5), (4, 0)):
+        st = gr.gr_multisplit_state(key=keys.data_ptr(), base=0, delta=delta, buckets=buckets,
+                                    bucket_len=blen.data_ptr())
+        with pytest.raises(gr.GrError):
+            gr.gr_filter(G.handle, items, 4, out, ol, mode=gr.GR_FILTER_MULTISPLIT, state=st)
+
+
 def test_operators_compose_into_bfs(gr, rmat14):
     """advance(BFS_VISIT, idempotent) + filter(EXACT_UNIQUE) per level == queue BFS."""
     g, G = rmat14

@@ -3,8 +3,9 @@
 A Poisson trace over eight small resident graphs (R-MAT and grids) runs
 through the continuous-batching loop (several lanes overlapping, BFS
 requests on the R-MAT graphs grouped into multi-source units, a memory
-budget that forces evictions) and through the serial plain path; each
-result must equal the CPU oracle's answer for that request.
+budget that forces evictions, released in each lane's stream order) and
+through the serial plain path; each result must equal the CPU oracle's
+answer for that request, and lanes must still overlap under evictions.
 """
 import numpy as np
 import pytest
@@ -49,6 +50,12 @@ def test_served_results_equal_solo_results(setup):
         2 * max(i.bytes_sssp for i in infos.values())
     stats = serve.serve_trace(be, trace, 3, budget, multi_names=multi)
     assert stats["completed"] == len(trace) and stats["errors"] == 0
+    # the budget forced evictions (released in stream order), and lanes still overlapped:
+    # some requests on different lanes ran at the same time
+    assert stats["evictions"] > 0 and be.evicted > 0
+    overlap = any(a.lane != b.lane and a.t_start < b.t_done and b.t_start < a.t_done
+                  for a in trace for b in trace)
+    assert overlap
     grouped = 0
     for r in trace:
         want = expected(csrs[r.graph], r.op, r.src)

@@ -79,7 +79,9 @@ def test_step_stats(gr, s16w):
             assert (s[split, 2] > 0).all()    # near/far splits drain the far pile
         assert (s[~split, 0] > 0).all()
         assert (np.diff(s[:, 3]) >= 0).all()
-        assert (host(stats).reshape(cap, 4)[steps:] == -7).all()
+        end = host(stats).reshape(cap, 4)[steps]            # the loop's end row
+        assert end[0] == 0 and end[1] == 0 and end[2] == 0 and end[3] >= s[-1, 3]
+        assert (host(stats).reshape(cap, 4)[steps + 1:] == -7).all()
 
 
 @pytest.mark.parametrize("bulk", [-1, 1, 4096])
