@@ -171,6 +171,7 @@ static size_t ws_bytes(const gr_graph* g, int32_t ops) {
   b += n * sizeof(int32_t) + bw * sizeof(uint32_t);              // filter scratch
   b += (GR_MAX_SCAN_BLOCKS + 2) * sizeof(long long);             // scan scratch
   b += n * sizeof(int32_t) + 8 * sizeof(long long);              // pull tags, counters
+  b += GR_PULL_DEFER_INTS * sizeof(int32_t);                     // deferred pull rows
   b += n * sizeof(long long);                                    // advance offsets
   if (ops & GR_OP_SSSP) b += n * sizeof(uint64_t) + (5 + GR_RING_K) * n * sizeof(int32_t);
   return b;
@@ -220,7 +221,7 @@ static void ws_free(gr_workspace* ws, cudaStream_t s = nullptr) {
                   ws->chunks[0], ws->chunks[1],
                   ws->visited, ws->front[0], ws->front[1], ws->front[2], ws->key,
                   ws->far[0], ws->far[1], ws->stamp_near, ws->stamp_far, ws->first_idx,
-                  ws->claim, ws->block_sums, ws->tags, ws->item_off, ws->dev_len};
+                  ws->claim, ws->block_sums, ws->tags, ws->pdef, ws->item_off, ws->dev_len};
   for (void* p : ptrs) release(p);
   for (int j = 0; j < GR_RING_K; ++j) release(ws->ring[j]);
   release(ws->stamp_ring);
@@ -274,6 +275,7 @@ static gr_status ws_create(const gr_graph* g, int32_t ops, gr_workspace** out,
   ALLOC(ws->claim, bw * sizeof(uint32_t));
   ALLOC(ws->block_sums, (GR_MAX_SCAN_BLOCKS + 2) * sizeof(long long));
   ALLOC(ws->tags, n * sizeof(int32_t));
+  ALLOC(ws->pdef, GR_PULL_DEFER_INTS * sizeof(int32_t));
   ALLOC(ws->item_off, n * sizeof(long long));
   ALLOC(ws->dev_len, 8 * sizeof(long long));
   if (ops & GR_OP_SSSP) {

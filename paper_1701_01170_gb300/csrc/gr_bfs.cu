@@ -124,6 +124,7 @@ extern "C" gr_status gr_bfs(const gr_graph* g, int32_t src, int32_t* depth, int3
   a.bulk_edges = o.bulk_edges < 0 ? 0 : (o.bulk_edges > 0 ? o.bulk_edges
                                                           : gr_default_bulk_edges(g->n));
   a.preset = symmetric ? g->zero_deg : nullptr;
+  a.pdef = ws->pdef;
 
   bfs_carveout_once();
   int blocks = gr_launch_blocks((const void*)bfs_persistent, NT, 0, g->num_sms,
@@ -186,7 +187,9 @@ constexpr size_t kOffCh1 = kOffCh0 + kChunkBytes;
 constexpr size_t kBitmapBytes = round256((size_t)kStaticWords * sizeof(uint32_t));
 constexpr size_t kOffVisited = kOffCh1 + kChunkBytes;
 constexpr size_t kOffFront = kOffVisited + kBitmapBytes;
-constexpr size_t kStaticBytes = kOffFront + 3 * kBitmapBytes;  // about 13.1 MB
+constexpr size_t kOffPdef = kOffFront + 3 * kBitmapBytes;
+constexpr size_t kStaticBytes =
+    kOffPdef + round256(GR_PULL_DEFER_INTS * sizeof(int32_t));  // about 13.1 MB
 
 static __device__ __align__(256) unsigned char g_bfs_static_scratch[kStaticBytes];
 
@@ -272,6 +275,7 @@ extern "C" gr_status gr_bfs_static(int32_t n, int64_t m, const int32_t* row_offs
   a.level_stats = nullptr;
   a.max_levels = 0;
   a.bulk_edges = gr_default_bulk_edges(n);
+  a.pdef = (int32_t*)(base + kOffPdef);
 
   // the control block and the status word must start at zero; the rest of
   // the scratch is initialised by the kernel itself

@@ -58,6 +58,8 @@ struct BfsArgs {
                        // (0: never); needs the frontier bitmaps front[]
   const uint32_t* preset;  // n-bit bitmap of vertices that start as visited (isolated vertices
                            // of a symmetric graph, which no edge reaches) or NULL
+  int32_t* pdef;  // GR_PULL_DEFER_INTS entries: long pull rows shared by the grid (NULL: each
+                  // row is scanned by the warp that owns its vertex)
 };
 
 // The whole BFS (init + level loop) for one query, executed by the threads
@@ -126,6 +128,7 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
   GrBigStage bstage{ar.bv, ar.bb, ar.bd, ar.bo, &s_bcnt, s_btot};
   __shared__ unsigned long long s_mfsum;
   __shared__ int s_found;
+  __shared__ int s_ndef;  // rows the previous level deferred to the grid
   int list_ready = 0;  // the previous level was a pull level that wrote an unvisited list
   int pull = 0;
   int prev_pull = 0;   // the previous level was a pull level: its frontier exists as a bitmap only
@@ -139,6 +142,7 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
       s_nbig = __ldcg(&ctl->nbig[s0]);
       s_mf = __ldcg(&ctl->mf[s0]);
       s_nu = __ldcg(&ctl->ulen[s0]);
+      s_ndef = a.pdef && L > 0 ? __ldcg(&ctl->ndef[s2]) : 0;
       stage.reset();
       mstage.reset();
       ustage.reset();
@@ -147,6 +151,81 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
       s_found = 0;
     }
     __syncthreads();
+    // ---- rows the previous (pull) level deferred to the whole grid --------
+    // Each listed row (vertex, first edge, end edge, chunks done, degree) is
+    // cut into GR_PULL_CHUNK-edge chunks dealt out to the warps in turn.  The
+    // first frontier neighbour a chunk finds claims the vertex (CAS on its
+    // depth) for the previous level, whose frontier bitmap front[s2] is still
+    // intact and whose counters (slot s0) the level below reads only after
+    // the barrier; a chunk that starts after the claim skips its scan.  The
+    // warp that completes a row's last chunk keeps the vertex on the
+    // unvisited list if nothing matched.  The list's length was written
+    // before the last barrier and is read with the level's other counters,
+    // so every warp takes the same branch.
+    if (s_ndef > 0) {
+      {
+        const int nd = min(s_ndef, GR_PULL_DEFER_CAP);
+        const uint32_t* fprev = a.front[s2];
+        uint32_t* fcur = a.front[s0];
+        int32_t* ulist = a.ulist[0] ? a.ulist[L & 1] : nullptr;
+        int64_t base = 0;
+        for (int d = 0; d < nd; ++d) {
+          int32_t* ent = a.pdef + 8 * d;
+          const int32_t v = __ldcg(ent), beg = __ldcg(ent + 1), end = __ldcg(ent + 2);
+          const int nchd = (end - beg + GR_PULL_CHUNK - 1) / GR_PULL_CHUNK;
+          // this warp's chunks of the row: global chunk indices = swarp (mod nwarps)
+          int64_t c = base + ((swarp - base) % nwarps + nwarps) % nwarps;
+          for (; c < base + nchd; c += nwarps) {
+            int32_t claimed = 0;
+            if (lane == 0) claimed = __ldcg(a.depth + v) >= 0;
+            if (!__shfl_sync(GR_FULL_MASK, claimed, 0)) {
+              const int cb = beg + (int)(c - base) * GR_PULL_CHUNK;
+              const int ce = min(cb + GR_PULL_CHUNK, end);
+              constexpr int J = GR_PULL_CHUNK / 32;
+              int32_t u[J];
+#pragma unroll
+              for (int j = 0; j < J; ++j) {
+                const int e = cb + j * 32 + lane;
+                u[j] = e < ce ? __ldg(a.C + e) : -1;
+                if (u[j] >= 0) ++cnt.edges;
+              }
+              int32_t hu = -1;
+#pragma unroll
+              for (int j = J - 1; j >= 0; --j)
+                if (u[j] >= 0 && ((fprev[u[j] >> 5] >> (u[j] & 31)) & 1u)) hu = u[j];
+              const unsigned hm = __ballot_sync(GR_FULL_MASK, hu >= 0);
+              if (hm) {
+                const int32_t par = __shfl_sync(GR_FULL_MASK, hu, __ffs(hm) - 1);
+                if (lane == 0 && atomicCAS(a.depth + v, -1, L) == -1) {
+                  ++cnt.updates;
+                  if (a.pred) a.pred[v] = par;
+                  atomicOr(a.visited + (v >> 5), 1u << (v & 31));
+                  atomicOr(fcur + (v >> 5), 1u << (v & 31));
+                  atomicAdd(&ctl->qlen[s0], 1);
+                  atomicAdd(&ctl->mf[s0], (unsigned long long)__ldcg(ent + 5));
+                }
+              }
+            }
+            if (lane == 0) {
+              __threadfence();
+              if (atomicAdd(ent + 3, 1) + 1 == nchd && ulist && __ldcg(a.depth + v) < 0) {
+                const int pos = atomicAdd(&ctl->ulen[s0], 1);
+                if (pos < a.n) ulist[pos] = v;
+              }
+            }
+          }
+          base += nchd;
+        }
+        if (!sc.sync()) return;
+      }
+      // the counters of this level, now with the deferred rows' outcomes
+      if (threadIdx.x == 0) {
+        s_nq = __ldcg(&ctl->qlen[s0]);
+        s_mf = __ldcg(&ctl->mf[s0]);
+        s_nu = __ldcg(&ctl->ulen[s0]);
+      }
+      __syncthreads();
+    }
     // after a pull level qlen counts the discovered vertices without
     // listing them (the level's frontier is its bitmap)
     int nq = min(s_nq, a.n);
@@ -186,6 +265,7 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
       ctl->workb[s2] = 0;
       ctl->qbuilt[s2] = 0;
       ctl->ulen[s2] = 0;
+      ctl->ndef[s1] = 0;  // (slot s2 holds the deferred rows of the previous level)
     }
     if (bitmaps)
       for (int64_t w = gtid; w < a.nwords; w += gthreads) a.front[s2][w] = 0u;
@@ -403,9 +483,13 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
       // First frontier neighbour in row order of each lane's candidate, or -1.
       // Each lane scans its first GR_PULL_SERIAL neighbours alone (rows are
       // sorted, so hubs come first and most candidates stop early); longer
-      // rows that still need more are then scanned by the whole warp, 32
-      // neighbours a round.  All 32 lanes call.
-      auto find_parent = [&](bool cand, int beg, int deg) -> int32_t {
+      // rows that still need more are then scanned by the whole warp, 128
+      // neighbours a round; a row still unresolved after GR_PULL_WARP_EDGES
+      // more, with GR_PULL_DEFER_MIN or more left, goes to the deferred list
+      // (GR_PULL_DEFERRED), which every warp of the grid finishes at the top
+      // of the next level.  v and vdeg are the candidate and its full
+      // degree.  All 32 lanes call.
+      auto find_parent = [&](bool cand, int beg, int deg, int32_t v, int vdeg) -> int32_t {
         int32_t found = -1;
         const int p = cand ? min(deg, GR_PULL_SERIAL) : 0;
         // four neighbours per round: their column and bitmap loads overlap
@@ -429,17 +513,48 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
           pending &= pending - 1u;
           const int lb = __shfl_sync(GR_FULL_MASK, beg, l);
           const int le = lb + __shfl_sync(GR_FULL_MASK, deg, l);
+          const int32_t vl = __shfl_sync(GR_FULL_MASK, v, l);
+          const int dl = __shfl_sync(GR_FULL_MASK, vdeg, l);
           int32_t f = -1;
-          for (int e0 = lb + GR_PULL_SERIAL; e0 < le; e0 += 32) {
-            const int e = e0 + lane;
-            const bool ok = e < le;
-            const int32_t u = ok ? __ldg(a.C + e) : 0;
-            if (ok) ++cnt.edges;
-            const unsigned hm = __ballot_sync(GR_FULL_MASK, ok && ((fcur[u >> 5] >> (u & 31)) & 1u));
-            if (hm) {
-              f = __shfl_sync(GR_FULL_MASK, u, __ffs(hm) - 1);
-              break;
+          bool may_defer = a.pdef != nullptr;
+          for (int e0 = lb + GR_PULL_SERIAL; e0 < le; e0 += 128) {
+            if (may_defer && e0 - lb >= GR_PULL_SERIAL + GR_PULL_WARP_EDGES &&
+                le - e0 >= GR_PULL_DEFER_MIN) {  // warp-uniform
+              int slot = 0;
+              if (lane == 0) slot = atomicAdd(&ctl->ndef[s0], 1);
+              slot = __shfl_sync(GR_FULL_MASK, slot, 0);
+              if (slot < GR_PULL_DEFER_CAP) {
+                if (lane == 0) {
+                  int32_t* ent = a.pdef + 8 * slot;
+                  ent[0] = vl;
+                  ent[1] = e0;
+                  ent[2] = le;
+                  ent[3] = 0;  // chunks done
+                  ent[5] = dl;
+                }
+                f = GR_PULL_DEFERRED;
+                break;
+              }
+              may_defer = false;  // the list is full: this warp scans on
             }
+            // 128 neighbours a round, four loads per lane in flight; the
+            // first hit in row order is the lowest (j, lane)
+            int32_t u[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int e = e0 + j * 32 + lane;
+              u[j] = e < le ? __ldg(a.C + e) : -1;
+              if (u[j] >= 0) ++cnt.edges;
+            }
+            bool in[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) in[j] = u[j] >= 0 && ((fcur[u[j] >> 5] >> (u[j] & 31)) & 1u);
+#pragma unroll
+            for (int j = 0; j < 4 && f < 0; ++j) {
+              const unsigned hm = __ballot_sync(GR_FULL_MASK, in[j]);
+              if (hm) f = __shfl_sync(GR_FULL_MASK, u[j], __ffs(hm) - 1);
+            }
+            if (f >= 0) break;
           }
           if (lane == l) found = f;
         }
@@ -459,7 +574,9 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
         const unsigned fm = __ballot_sync(GR_FULL_MASK, found >= 0);
         if (lane == 0 && fm) atomicAdd(&s_found, __popc(fm));
         // a vertex that can still be discovered stays on the unvisited list
-        if (unext) ustage.append(unext, &ctl->ulen[s1], a.n, valid && found < 0 && deg > 0, v, lane);
+        // (a deferred one is listed, if still unmatched, by its last chunk at
+        // the top of the next level)
+        if (unext) ustage.append(unext, &ctl->ulen[s1], a.n, valid && found == -1 && deg > 0, v, lane);
       };
       // A lane holds GR_PULL_WORDS candidates at once: their row bounds and
       // first neighbours are loaded together (independent loads in flight),
@@ -508,7 +625,8 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
 #pragma unroll
           for (int k = 0; k < K; ++k) {
             int32_t found = f0[k];
-            const int32_t rest = find_parent(cand[k] && found < 0 && deg[k] > 1, beg[k] + 1, deg[k] - 1);
+            const int32_t rest = find_parent(cand[k] && found < 0 && deg[k] > 1, beg[k] + 1, deg[k] - 1,
+                                             v[k], deg[k]);
             if (found < 0) found = rest;
             // list entries are distinct vertices: set their bits, one atomic per word
             gr_warp_set_bit(a.visited, found >= 0, v[k], lane);
@@ -538,9 +656,12 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
           for (int k = 0; k < K; ++k) {
             if (word[k] == 0xffffffffu) continue;  // warp-uniform
             int32_t found = f0[k];
-            const int32_t rest = find_parent(cand[k] && found < 0 && deg[k] > 1, beg[k] + 1, deg[k] - 1);
+            const int32_t rest = find_parent(cand[k] && found < 0 && deg[k] > 1, beg[k] + 1, deg[k] - 1,
+                                             v[k], deg[k]);
             if (found < 0) found = rest;
             // the warp owns this word: visited and next-frontier bits by ballot
+            // (a deferred vertex of the word gets its bits after the level's
+            // barrier)
             const unsigned hit = __ballot_sync(GR_FULL_MASK, found >= 0);
             if (hit != 0u && lane == 0) {
               a.visited[wb + k] = word[k] | hit;

@@ -79,6 +79,7 @@ struct GrCtl {
   int qbuilt[3];                   // BFS: queue rows rebuilt from a pull level's bitmap
   int qmlen[3];                    // medium-row queue length, slot = step % 3
   int workm[3];                    // dynamic work counter (medium-row batches)
+  int ndef[3];                     // BFS pull: rows deferred to the whole grid, slot = level % 3
   unsigned farmin[3];              // SSSP smallest distance pushed to a far pile
   int rlen[GR_RING_K];             // SSSP multi-level queue: entries of each ring slot
   int ovf_pending;                 // SSSP: some relaxation sum did not fit in 32 bits
@@ -169,6 +170,7 @@ struct gr_workspace {
   uint32_t* claim;      // filter scratch: n bits, 0 when clean
   long long* block_sums;// operator scan scratch, GR_MAX_SCAN_BLOCKS + 2 entries
   int32_t* tags;        // pull scratch: n entries
+  int32_t* pdef;        // BFS pull: deferred long rows, GR_PULL_DEFER_INTS entries
   long long* item_off;  // advance scratch: n + 1 per-item output offsets
   long long* dev_len;   // operator scratch: a few device counters
   GrBcScratch* bc;      // allocated by the first gr_bc call on this workspace
@@ -321,6 +323,23 @@ __device__ __forceinline__ int gr_next_batch(int cur, int total, int static_span
 #ifndef GR_PULL_SERIAL
 #define GR_PULL_SERIAL 64  // neighbours a pull candidate scans alone before the warp helps
 #endif
+// A pull candidate whose row shows no frontier neighbour in its first
+// GR_PULL_SERIAL + GR_PULL_WARP_EDGES entries, with at least GR_PULL_DEFER_MIN
+// more to go, is handed to the whole grid: the rest of its row is cut into
+// GR_PULL_CHUNK-edge chunks that all warps share at the top of the next level
+// (at most GR_PULL_DEFER_CAP such rows per level; beyond that the warp scans
+// on alone).  Each entry of the deferred list is 8 int32: vertex, first edge,
+// end edge, chunks done, unused, degree, unused, unused.
+#ifndef GR_PULL_WARP_EDGES
+#define GR_PULL_WARP_EDGES 1024
+#endif
+#ifndef GR_PULL_DEFER_MIN
+#define GR_PULL_DEFER_MIN 1024
+#endif
+#define GR_PULL_CHUNK 256
+#define GR_PULL_DEFERRED (-2)  // find_parent: the row went to the deferred list
+#define GR_PULL_DEFER_CAP 1024
+#define GR_PULL_DEFER_INTS (8 * GR_PULL_DEFER_CAP)
 #define GR_DIRECT_CLAIM_FRONTIER 32768  // below this frontier size (and twice as many
                                         // frontier edges) BFS claims without a pre-read
 

@@ -155,6 +155,48 @@ def test_frontier_grows_and_shrinks(gr, direction):
     G.close()
 
 
+def hubs_behind_a_path(fill=3000, hubs=1200, plen=6):
+    """A path 0 - p1 - ... - p_plen on the highest ids, `fill` leaves on ids
+    1..fill hanging off the path's end, and `hubs` hubs that each see every
+    leaf and one path vertex.  Rows are sorted, so a hub's path neighbour is
+    its last entry: on pull levels every hub scans its whole row of fill + 1
+    entries, long enough to go to the grid-shared deferred list; the hubs of
+    later path vertices stay unmatched for several levels, and more hubs than
+    the list holds are candidates at once."""
+    n = 1 + fill + hubs + plen
+    path = [0] + [n - 1 - i for i in range(plen)]
+    pairs = [(path[i], path[i + 1]) for i in range(plen)]
+    leaves = np.arange(1, fill + 1)
+    pairs += [(int(x), path[-1]) for x in leaves]
+    h = np.arange(fill + 1, fill + 1 + hubs)
+    hp = np.repeat(h, fill)
+    lp = np.tile(leaves, hubs)
+    pairs = np.concatenate([np.asarray(pairs, np.int64), np.stack([hp, lp], 1),
+                            np.stack([h, [path[1 + j % plen] for j in range(hubs)]], 1)])
+    return undirected(n, pairs)
+
+
+@pytest.mark.parametrize("direction", [0, 2])
+def test_long_unvisited_rows_are_shared_by_the_grid(gr, direction):
+    # pull levels (forced with direction 2) where hundreds of long rows end in
+    # their only frontier neighbour: matched ones, unmatched ones that stay
+    # listed for the next level, and more than the deferred list holds
+    import torch
+    g = hubs_behind_a_path()
+    G = gr.Graph.from_csr(g)
+    cap = 64
+    stats = torch.zeros(4 * cap, dtype=torch.int32, device="cuda")
+    d, p = run_bfs(gr, G, 0, direction=direction, level_stats=stats.data_ptr(), max_levels=cap)
+    check(g, 0, d, p)
+    levels = int(d.max()) + 1
+    s = host(stats).reshape(cap, 4)
+    assert np.array_equal(s[:levels, 0], np.bincount(d[d >= 0], minlength=levels))
+    for src in (g.n - 1, 5):
+        d, p = run_bfs(gr, G, src, direction=direction)
+        check(g, src, d, p)
+    G.close()
+
+
 def test_directed_graph_push_only(gr):
     rng = np.random.default_rng(3)
     n = 3000

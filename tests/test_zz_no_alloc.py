@@ -14,7 +14,7 @@ import pytest
 
 import graphgen as gg
 import oracle
-from _helpers import host
+from _helpers import host, star_plus
 
 pytestmark = pytest.mark.gpu
 
@@ -52,6 +52,20 @@ def test_static_bfs_matches_the_oracle_on_consecutive_calls(gr):
             assert np.array_equal(depth, want)
             assert np.array_equal(depth, host(ref))
             assert oracle.bfs_certificate(g.R, g.C, src, depth, pred) == 0
+    G.close()
+
+
+def test_static_bfs_shares_long_pull_rows(gr):
+    # from the second hub, the first hub's 300,000-entry row has no frontier
+    # neighbour on the first pull level: the static scratch's deferred list
+    # spreads it over the grid, and its later match must still be exact
+    g = star_plus(300_000)
+    G = gr.Graph.from_csr(g)
+    for src in (g.n - 1, 0, 1, g.n - 1):
+        depth, pred = static_bfs(gr, G, g, src, gr.GR_SYMMETRIC)
+        want, _ = oracle.bfs(g.R, g.C, src)
+        assert np.array_equal(depth, want)
+        assert oracle.bfs_certificate(g.R, g.C, src, depth, pred) == 0
     G.close()
 
 
