@@ -167,18 +167,42 @@ struct ExpandArgs {
   int32_t* pred;
   int32_t level;
   unsigned long long* key;
+  // first item of each output tile (adv_tile_map), for tiles t < tile_cap
+  const int32_t* tile_item;
+  int64_t tile_cap;
 };
 
 // Output-balanced expansion over output tiles: a CTA owns GR_ADV_TILE
-// consecutive output positions at a time.  One thread finds the tile's first
-// and last input items (two binary searches over the scanned offsets); the
-// items in between — their offsets, vertex ids and row starts — are staged in
-// shared memory, and every output position then finds its item with a search
-// in shared memory.  A warp's 32 outputs are consecutive positions, so the
-// column loads and the output stores are coalesced.  A tile that spans more
-// items than the stage holds (a run of empty rows) searches global memory.
+// consecutive output positions at a time.  The tile's first input item comes
+// from the tile map (the item holding the tile's first position, written by
+// adv_tile_map in one pass over the items), its last from the next tile's
+// entry; the items in between — their offsets, vertex ids and row starts —
+// are staged in shared memory, and every output position then finds its item
+// with a search in shared memory.  A warp's 32 outputs are consecutive
+// positions, so the column loads and the output stores are coalesced.  Tiles
+// beyond the map's capacity find their items with binary searches over the
+// scanned offsets, and a tile that spans more items than the stage holds (a
+// run of empty rows) searches global memory per position.
 #define GR_ADV_PER_THREAD 8
 #define GR_ADV_TILE (T * GR_ADV_PER_THREAD)
+
+// tile_item[t] = the item holding output position t * GR_ADV_TILE (the
+// largest item whose offset is at most that position), for every tile t <
+// tile_cap that starts below the total.  Only items that own positions write.
+__global__ void adv_tile_map(const long long* item_off, const long long* block_sums,
+                             int64_t len_host, const int64_t* len_dev, const long long* total,
+                             int32_t* tile_item, int64_t tile_cap) {
+  const int64_t len = eff_len(len_dev, len_host);
+  const long long tot = *total;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const long long o = item_offset(item_off, block_sums, i);
+    const long long o1 = i + 1 < len ? item_offset(item_off, block_sums, i + 1) : tot;
+    for (long long t = (o + GR_ADV_TILE - 1) / GR_ADV_TILE;
+         t < tile_cap && t * GR_ADV_TILE < o1; ++t)
+      tile_item[t] = (int32_t)i;
+  }
+}
 template <int FN>
 __global__ void adv_expand(ExpandArgs a) {
   __shared__ long long s_off[GR_ADV_TILE + 1];
@@ -194,8 +218,15 @@ __global__ void adv_expand(ExpandArgs a) {
        t0 += (long long)gridDim.x * GR_ADV_TILE) {
     const long long tend = min(t0 + (long long)GR_ADV_TILE, limit);
     if (threadIdx.x == 0) {
-      const int64_t i0 = search_item(a.item_off, a.block_sums, 0, len - 1, t0);
-      const int64_t i1 = search_item(a.item_off, a.block_sums, i0, len - 1, tend - 1);
+      const long long t = t0 / GR_ADV_TILE;
+      const int64_t i0 = t < a.tile_cap ? (int64_t)a.tile_item[t]
+                                        : search_item(a.item_off, a.block_sums, 0, len - 1, t0);
+      // the item holding the next tile's first position bounds this tile's
+      // last item (staged one too many at most, which no position selects)
+      int64_t i1;
+      if (tend >= total) i1 = len - 1;
+      else if (t + 1 < a.tile_cap) i1 = (int64_t)a.tile_item[t + 1];
+      else i1 = search_item(a.item_off, a.block_sums, i0, len - 1, tend - 1);
       s_i0 = i0;
       s_ni = i1 - i0 + 1;
     }
@@ -406,35 +437,189 @@ __global__ void compact_scatter(CompactArgs a) {
   }
 }
 
+// Single-pass ordered compaction (decoupled look-back).  A CTA takes the
+// next tile in launch order from a counter, classifies its items, publishes
+// the tile's counts, then derives its output offsets from its predecessors:
+// warp 0 reads their flag words 32 at a time and adds counts until it meets a
+// published prefix.  A predecessor holds an earlier tile, so it is already
+// running and publishes its counts before it looks back itself; the wait for
+// it is still bounded (GR_ERR_TIMEOUT in the status word after `spin` polls).
+// Flag word per tile: bits 63..62 state (0 none, 1 counts, 2 prefix), bits
+// 61..31 the first output's count, bits 30..0 the second output's.
+#define GR_LB_COUNTS 1ull
+#define GR_LB_PREFIX 2ull
+__device__ __forceinline__ unsigned long long lb_pack(unsigned long long st, long long c1,
+                                                      long long c2) {
+  return (st << 62) | ((unsigned long long)c1 << 31) | (unsigned long long)c2;
+}
+__device__ __forceinline__ unsigned long long lb_load(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void lb_store(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+template <int CL>
+__global__ void compact_onepass(CompactArgs a, unsigned long long* flags, int* tile_ctr,
+                                int64_t tiles, unsigned spin) {
+  __shared__ int s_tile;
+  __shared__ long long s_ex1, s_ex2;
+  if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1);
+  __syncthreads();
+  const int64_t tile = s_tile;
+  const int64_t len = CL == CL_UNVISITED ? a.n : eff_len(a.len_dev, a.len_host);
+  const int64_t base = tile * TILE + (int64_t)threadIdx.x * ITEMS;
+  unsigned char cls[ITEMS];
+  long long c1 = 0, c2 = 0;
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    const int64_t i = base + k;
+    cls[k] = i < len ? (unsigned char)classify<CL, true>(a, i) : (unsigned char)0;
+    c1 += cls[k] == 1;
+    c2 += cls[k] == 2;
+  }
+  long long t1, t2 = 0;
+  long long o1 = block_excl_scan<T>(c1, &t1);
+  long long o2 = 0;
+  if (CL == CL_NEAR_FAR) o2 = block_excl_scan<T>(c2, &t2);
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    long long ex1 = 0, ex2 = 0;
+    if (tile > 0) {
+      if (lane == 0) lb_store(flags + tile, lb_pack(GR_LB_COUNTS, t1, t2));
+      bool failed = false;
+      unsigned polls = 0;
+      for (int64_t p = tile - 1;; p -= 32) {
+        const int64_t idx = p - lane;
+        unsigned long long w = idx >= 0 ? lb_load(flags + idx) : lb_pack(GR_LB_PREFIX, 0, 0);
+        while (!__all_sync(GR_FULL_MASK, (w >> 62) != 0ull)) {
+          if (++polls > spin) {
+            failed = true;
+            break;
+          }
+          __nanosleep(32);
+          if ((w >> 62) == 0ull) w = lb_load(flags + idx);
+        }
+        if (failed) break;
+        const unsigned pm = __ballot_sync(GR_FULL_MASK, (w >> 62) == GR_LB_PREFIX);
+        const int stop = pm ? __ffs(pm) - 1 : 31;  // the nearest prefix ends the walk
+        long long v1 = lane <= stop ? (long long)((w >> 31) & 0x7fffffffull) : 0;
+        long long v2 = lane <= stop ? (long long)(w & 0x7fffffffull) : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          v1 += __shfl_xor_sync(GR_FULL_MASK, v1, o);
+          v2 += __shfl_xor_sync(GR_FULL_MASK, v2, o);
+        }
+        ex1 += v1;
+        ex2 += v2;
+        if (pm) break;
+      }
+      if (failed && lane == 0) gr_set_status(a.status, GR_ERR_TIMEOUT);
+    }
+    if (lane == 0) {
+      lb_store(flags + tile, lb_pack(GR_LB_PREFIX, ex1 + t1, ex2 + t2));
+      s_ex1 = ex1;
+      s_ex2 = ex2;
+    }
+  }
+  __syncthreads();
+  o1 += s_ex1;
+  o2 += s_ex2;
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    const int64_t i = base + k;
+    if (cls[k] == 1) {
+      const int32_t v = CL == CL_UNVISITED ? (int32_t)i : a.in[i];
+      if (o1 < a.cap) a.out[o1] = v;
+      ++o1;
+    } else if (cls[k] == 2) {
+      if (o2 < a.far_cap) a.far[o2] = a.in[i];
+      ++o2;
+    }
+  }
+  if (tile == tiles - 1 && threadIdx.x == 0) {
+    const long long tot1 = s_ex1 + t1;
+    *a.out_len = (unsigned long long)tot1;
+    if (tot1 > a.cap) gr_set_status(a.status, GR_ERR_CAPACITY);
+    if (CL == CL_NEAR_FAR) {
+      const long long tot2 = s_ex2 + t2;
+      *a.far_len = (unsigned long long)tot2;
+      if (tot2 > a.far_cap) gr_set_status(a.status, GR_ERR_CAPACITY);
+    }
+  }
+}
+
 __global__ void unique_mark_first(const int32_t* in, int64_t len_host, const int64_t* len_dev,
                                   int32_t n, int32_t* first_idx) {
   int64_t len = eff_len(len_dev, len_host);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
        i += (int64_t)gridDim.x * blockDim.x) {
     int32_t v = in[i];
-    if (v >= 0 && v < n) atomicMin(&first_idx[v], (int32_t)i);
+    // the index only ever decreases: skip the reduction when an earlier
+    // occurrence already holds a smaller one (a stale cached value only
+    // costs an unnecessary reduction)
+    if (v >= 0 && v < n && first_idx[v] > (int32_t)i) atomicMin(&first_idx[v], (int32_t)i);
   }
 }
 
 // CULL: claim each id once in a bitmap; emit the claimants (order unspecified).
+// A CTA takes GR_CULL_ROUND items a round, stages its claimants in shared
+// memory (one shared atomic per warp and pass) and reserves their output
+// range with one global atomic per round, so the output counter sees tens of
+// thousands of atomics instead of one per warp with a claimant.  Claimants
+// past the capacity are released at once (their bits cleared), so that the
+// claim bitmap is clean again after the call either way.
+#define GR_CULL_PER_THREAD 8
+#define GR_CULL_ROUND (T * GR_CULL_PER_THREAD)
 __global__ void cull_claim(const int32_t* in, int64_t len_host, const int64_t* len_dev, int32_t n,
                            uint32_t* claim, int32_t* out, int64_t cap,
                            unsigned long long* out_len, int* status) {
-  int64_t len = eff_len(len_dev, len_host);
-  int lane = threadIdx.x & 31;
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < len; i0 += stride) {
-    int64_t i = i0 + threadIdx.x;
-    bool take = false;
-    int32_t v = 0;
-    if (i < len) {
-      v = in[i];
-      if (v >= 0 && v < n) {
-        uint32_t bit = 1u << (v & 31);
-        if (!(claim[v >> 5] & bit)) take = !(atomicOr(&claim[v >> 5], bit) & bit);
+  __shared__ int32_t s_buf[GR_CULL_ROUND];
+  __shared__ int s_cnt;
+  __shared__ unsigned long long s_base;
+  const int64_t len = eff_len(len_dev, len_host);
+  const int lane = threadIdx.x & 31;
+  for (int64_t r0 = (int64_t)blockIdx.x * GR_CULL_ROUND; r0 < len;
+       r0 += (int64_t)gridDim.x * GR_CULL_ROUND) {
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    int32_t v[GR_CULL_PER_THREAD];
+#pragma unroll
+    for (int k = 0; k < GR_CULL_PER_THREAD; ++k) {
+      const int64_t i = r0 + (int64_t)k * T + threadIdx.x;
+      v[k] = i < len ? in[i] : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < GR_CULL_PER_THREAD; ++k) {
+      bool take = false;
+      if (v[k] >= 0 && v[k] < n) {
+        const uint32_t bit = 1u << (v[k] & 31);
+        if (!(claim[v[k] >> 5] & bit)) take = !(atomicOr(&claim[v[k] >> 5], bit) & bit);
+      }
+      const unsigned mask = __ballot_sync(GR_FULL_MASK, take);
+      if (mask) {
+        int base = 0;
+        if (lane == __ffs(mask) - 1) base = atomicAdd(&s_cnt, __popc(mask));
+        base = __shfl_sync(GR_FULL_MASK, base, __ffs(mask) - 1);
+        if (take) s_buf[base + __popc(mask & ((1u << lane) - 1u))] = v[k];
       }
     }
-    warp_append64(out, out_len, cap, take, v, lane, status);
+    __syncthreads();
+    const int cnt = s_cnt;
+    if (threadIdx.x == 0) {
+      s_base = cnt ? atomicAdd(out_len, (unsigned long long)cnt) : 0ull;
+      if (cnt && s_base + cnt > (unsigned long long)cap) gr_set_status(status, GR_ERR_CAPACITY);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += T) {
+      const unsigned long long pos = s_base + j;
+      const int32_t x = s_buf[j];
+      if (pos < (unsigned long long)cap) out[pos] = x;
+      else atomicAnd(&claim[x >> 5], ~(1u << (x & 31)));
+    }
+    __syncthreads();  // the next round reuses the stage
   }
 }
 
@@ -450,6 +635,21 @@ __global__ void cull_release(const int32_t* out, const unsigned long long* out_l
 }
 
 int64_t tiles_for(int64_t len) { return (len + TILE - 1) / TILE; }
+
+// look-back polls before a tile gives up on a predecessor (each poll sleeps
+// about 32 ns, so about a second)
+constexpr unsigned kLookbackPolls = 1u << 25;
+
+template <int CL>
+gr_status launch_onepass(const CompactArgs& a, gr_workspace* ws, int64_t tiles, cudaStream_t s) {
+  unsigned long long* flags = (unsigned long long*)ws->block_sums;
+  int* ctr = (int*)(ws->dev_len + 6);
+  if (cudaMemsetAsync(flags, 0, (size_t)tiles * sizeof(unsigned long long), s) != cudaSuccess ||
+      cudaMemsetAsync(ctr, 0, sizeof(int), s) != cudaSuccess)
+    return GR_ERR_CUDA;
+  compact_onepass<CL><<<(unsigned)tiles, T, 0, s>>>(a, flags, ctr, tiles, kLookbackPolls);
+  return cudaGetLastError() == cudaSuccess ? GR_OK : GR_ERR_CUDA;
+}
 
 }  // namespace
 
@@ -527,6 +727,15 @@ extern "C" gr_status gr_advance(const gr_graph* g, const int32_t* in, int64_t in
   a.R = g->R; a.C = g->C; a.W = g->W; a.in = in; a.len_host = in_len; a.len_dev = in_len_dev;
   a.item_off = item_off; a.block_sums = ws->block_sums; a.total = ws->dev_len; a.out = out;
   a.cap = out_cap; a.out_len = olen; a.status = ws->status;
+  // the tile map lives in the pull scratch (n + 1 entries: every tile of an
+  // expansion of up to (n + 1) * GR_ADV_TILE outputs)
+  a.tile_item = ws->tags;
+  a.tile_cap = (int64_t)g->n + 1;
+  {
+    const int64_t mb = (in_len + T - 1) / T;
+    adv_tile_map<<<(unsigned)(mb < 4096 ? mb : 4096), T, 0, s>>>(
+        item_off, ws->block_sums, in_len, in_len_dev, ws->dev_len, ws->tags, a.tile_cap);
+  }
   if (fn == FN_BFS || fn == FN_BFS_IDEM) {
     const gr_bfs_state* st = (const gr_bfs_state*)state;
     a.depth = st->depth; a.pred = st->pred; a.level = st->level;
@@ -565,6 +774,7 @@ struct MsplitArgs {
   int K;
   long long* counts;  // K x tiles, bucket-major (scanned in place between the passes)
   int64_t tiles;
+  signed char* bucket;  // tiles * TILE bytes: each item's bucket, -1 for none
   int32_t* out;
   int64_t cap;
   int* status;
@@ -579,47 +789,93 @@ __device__ __forceinline__ int msplit_bucket(const MsplitArgs& a, int32_t v) {
   return b >= (unsigned long long)(a.K - 1) ? a.K - 1 : (int)b;
 }
 
+// Per-thread bucket counts of ITEMS consecutive items, summed per warp
+// (shuffles) and per CTA (one shared atomic per warp and bucket).  The bucket
+// of every item is kept as a byte (ITEMS = 16 bytes a thread, one vector
+// store), so that the scatter pass reads bytes in order instead of gathering
+// the distances a second time.
 __global__ void msplit_count(MsplitArgs a) {
+  static_assert(ITEMS == 16, "one 16-byte vector of bucket bytes per thread");
   __shared__ int s_cnt[GR_RING_K];
   if (threadIdx.x < GR_RING_K) s_cnt[threadIdx.x] = 0;
   __syncthreads();
   const int64_t len = eff_len(a.len_dev, a.len_host);
   const int64_t base = (int64_t)blockIdx.x * TILE + (int64_t)threadIdx.x * ITEMS;
-  for (int k = 0; k < ITEMS && base + k < len; ++k) {
-    const int b = msplit_bucket(a, a.in[base + k]);
-    if (b >= 0) atomicAdd(&s_cnt[b], 1);
+  int c[GR_RING_K];
+#pragma unroll
+  for (int j = 0; j < GR_RING_K; ++j) c[j] = 0;
+  union {
+    signed char b[ITEMS];
+    uint4 v;
+  } bk;
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    bk.b[k] = base + k < len ? (signed char)msplit_bucket(a, a.in[base + k]) : (signed char)-1;
+#pragma unroll
+    for (int j = 0; j < GR_RING_K; ++j) c[j] += bk.b[k] == j;
+  }
+  if (base < len) reinterpret_cast<uint4*>(a.bucket)[base / ITEMS] = bk.v;
+#pragma unroll
+  for (int j = 0; j < GR_RING_K; ++j) {
+    int x = c[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(GR_FULL_MASK, x, o);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(&s_cnt[j], x);
   }
   __syncthreads();
   if (threadIdx.x < a.K) a.counts[(int64_t)threadIdx.x * a.tiles + blockIdx.x] = s_cnt[threadIdx.x];
 }
 
-// Each thread owns ITEMS consecutive items of the tile, so per-bucket block scans of
-// the threads' counts give every item its place after the earlier items of its bucket.
+// Each thread owns ITEMS consecutive items of the tile.  An item's place is
+// its bucket's start in this tile (the scanned counts) + the counts of that
+// bucket in the earlier warps of the CTA + in the earlier lanes of its warp
+// (warp scans of the per-thread counts) + the earlier items of the thread.
 __global__ void msplit_scatter(MsplitArgs a) {
+  constexpr int NW = T / 32;
+  __shared__ int s_wt[NW][GR_RING_K];  // per-warp bucket totals, then their exclusive scan
   const int64_t len = eff_len(a.len_dev, a.len_host);
   const int64_t base = (int64_t)blockIdx.x * TILE + (int64_t)threadIdx.x * ITEMS;
-  signed char bk[ITEMS];
-  int c[GR_RING_K];
-#pragma unroll
-  for (int j = 0; j < GR_RING_K; ++j) c[j] = 0;
-#pragma unroll
-  for (int k = 0; k < ITEMS; ++k) {
-    bk[k] = base + k < len ? (signed char)msplit_bucket(a, a.in[base + k]) : (signed char)-1;
-#pragma unroll
-    for (int j = 0; j < GR_RING_K; ++j) c[j] += bk[k] == j;
-  }
-  long long pos[GR_RING_K];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  union {
+    signed char b[ITEMS];
+    uint4 v;
+  } bk;
+  bk.v = base < len ? reinterpret_cast<const uint4*>(a.bucket)[base / ITEMS]
+                    : make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+  int pos[GR_RING_K];
 #pragma unroll
   for (int j = 0; j < GR_RING_K; ++j) {
-    long long tot;
-    const long long pre = block_excl_scan<T>(j < a.K ? c[j] : 0, &tot);
-    pos[j] = j < a.K ? a.counts[(int64_t)j * a.tiles + blockIdx.x] + pre : 0;
+    int c = 0;
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) c += bk.b[k] == j;
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(GR_FULL_MASK, incl, o);
+      if (lane >= o) incl += y;
+    }
+    pos[j] = incl - c;
+    if (lane == 31) s_wt[w][j] = incl;
   }
+  __syncthreads();
+  if (threadIdx.x < GR_RING_K) {
+    int run = 0;
+#pragma unroll
+    for (int x = 0; x < NW; ++x) {
+      const int t = s_wt[x][threadIdx.x];
+      s_wt[x][threadIdx.x] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < GR_RING_K; ++j)
+    if (j < a.K) pos[j] += (int)a.counts[(int64_t)j * a.tiles + blockIdx.x] + s_wt[w][j];
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
-    const int b = bk[k];
+    const int b = bk.b[k];
     if (b < 0) continue;
-    long long at = 0;
+    int at = 0;
 #pragma unroll
     for (int j = 0; j < GR_RING_K; ++j)
       if (j == b) at = pos[j]++;
@@ -664,12 +920,7 @@ extern "C" gr_status gr_filter(const gr_graph* g, const int32_t* in, int64_t in_
     if (!st || !st->depth) return GR_ERR_INVALID_ARG;
     a.depth = st->depth;
     if (g->n == 0) return cudaMemsetAsync(out_len, 0, 8, s) == cudaSuccess ? GR_OK : GR_ERR_CUDA;
-    int64_t tiles = tiles_for(g->n);
-    compact_count<CL_UNVISITED><<<(unsigned)tiles, T, 0, s>>>(a);
-    scan_block_sums<<<1, 1024, 0, s>>>(ws->block_sums, tiles, 0, ws->dev_len);
-    compact_scatter<CL_UNVISITED><<<(unsigned)tiles, T, 0, s>>>(a);
-    GR_LAUNCH_CHECK();
-    return GR_OK;
+    return launch_onepass<CL_UNVISITED>(a, ws, tiles_for(g->n), s);
   }
   if (mode == GR_FILTER_NEAR_FAR) {
     const gr_sssp_state* st = (const gr_sssp_state*)state;
@@ -680,16 +931,10 @@ extern "C" gr_status gr_filter(const gr_graph* g, const int32_t* in, int64_t in_
         return GR_ERR_CUDA;
       return GR_OK;
     }
-    if (tiles_for(in_len) > GR_MAX_SCAN_BLOCKS / 2) return GR_ERR_INVALID_ARG;
     a.key = (const unsigned long long*)st->key;
     a.threshold = st->threshold;
     a.far = far; a.far_cap = far_cap; a.far_len = (unsigned long long*)far_len;
-    int64_t tiles = tiles_for(in_len);
-    compact_count<CL_NEAR_FAR><<<(unsigned)tiles, T, 0, s>>>(a);
-    scan_block_sums<<<1, 1024, 0, s>>>(ws->block_sums, tiles, 1, ws->dev_len);
-    compact_scatter<CL_NEAR_FAR><<<(unsigned)tiles, T, 0, s>>>(a);
-    GR_LAUNCH_CHECK();
-    return GR_OK;
+    return launch_onepass<CL_NEAR_FAR>(a, ws, tiles_for(in_len), s);
   }
   if (mode == GR_FILTER_MULTISPLIT) {
     const gr_multisplit_state* st = (const gr_multisplit_state*)state;
@@ -707,18 +952,24 @@ extern "C" gr_status gr_filter(const gr_graph* g, const int32_t* in, int64_t in_
     m.key = (const unsigned long long*)st->key; m.base = st->base; m.delta = st->delta;
     m.K = st->buckets; m.tiles = tiles_for(in_len); m.out = out; m.cap = out_cap;
     m.status = ws->status;
+    // one temporary: the items' bucket bytes (a whole number of tiles), then
+    // the K x tiles counts
+    const size_t bbytes = (size_t)m.tiles * TILE;
     const size_t cbytes = (size_t)m.K * (size_t)m.tiles * sizeof(long long);
-    if (cudaMallocAsync((void**)&m.counts, cbytes, s) != cudaSuccess) {
+    unsigned char* tmp = nullptr;
+    if (cudaMallocAsync((void**)&tmp, bbytes + cbytes, s) != cudaSuccess) {
       (void)cudaGetLastError();
       return GR_ERR_OOM;
     }
+    m.bucket = (signed char*)tmp;
+    m.counts = (long long*)(tmp + bbytes);
     msplit_count<<<(unsigned)m.tiles, T, 0, s>>>(m);
     scan_block_sums<<<1, 1024, 0, s>>>(m.counts, (int64_t)m.K * m.tiles, 0, ws->dev_len);
     msplit_scatter<<<(unsigned)m.tiles, T, 0, s>>>(m);
     msplit_lens<<<1, 32, 0, s>>>(m.counts, m.tiles, m.K, ws->dev_len, st->bucket_len, olen,
                                  out_cap, ws->status);
     const bool launched = cudaGetLastError() == cudaSuccess;
-    if (cudaFreeAsync(m.counts, s) != cudaSuccess || !launched) {
+    if (cudaFreeAsync(tmp, s) != cudaSuccess || !launched) {
       (void)cudaGetLastError();
       return GR_ERR_CUDA;
     }
@@ -727,13 +978,9 @@ extern "C" gr_status gr_filter(const gr_graph* g, const int32_t* in, int64_t in_
   if (in_len == 0)
     return cudaMemsetAsync(out_len, 0, 8, s) == cudaSuccess ? GR_OK : GR_ERR_CUDA;
   if (mode == GR_FILTER_EXACT_UNIQUE) {
-    int64_t tiles = tiles_for(in_len);
     unique_mark_first<<<g->num_sms * 8, T, 0, s>>>(in, in_len, in_len_dev, g->n, ws->first_idx);
-    compact_count<CL_UNIQUE><<<(unsigned)tiles, T, 0, s>>>(a);
-    scan_block_sums<<<1, 1024, 0, s>>>(ws->block_sums, tiles, 0, ws->dev_len);
-    compact_scatter<CL_UNIQUE><<<(unsigned)tiles, T, 0, s>>>(a);
     GR_LAUNCH_CHECK();
-    return GR_OK;
+    return launch_onepass<CL_UNIQUE>(a, ws, tiles_for(in_len), s);
   }
   // GR_FILTER_CULL
   if (cudaMemsetAsync(out_len, 0, 8, s) != cudaSuccess) return GR_ERR_CUDA;
