@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(BT) batch_kernel(BatchArgs b, SlotLayout L) {
       a.do_b = J.do_b;
       a.spin = b.spin;
       a.bulk_edges = 0;  // batched graphs are small: every push level claims as it goes
-      gr_bfs_body(a, sc, ar);
+      gr_bfs_body<true>(a, sc, ar);
     } else {
       SsspArgs a = {};
       a.n = J.n;

@@ -36,11 +36,21 @@ constexpr int NT = GR_PERSIST_THREADS;
 #ifndef GR_BFS_MIN_BLOCKS
 #define GR_BFS_MIN_BLOCKS 2  // resident CTAs per SM the register budget is sized for
 #endif
+// Two instantiations: queries that may pull (direction-optimising or forced
+// pull, symmetric graphs) and push-only queries, whose kernel carries no pull
+// code at all (with the pull levels' code in the same loop, the push levels
+// of a push-only R-MAT s22 BFS ran 2-3 % slower).
+template <bool PULL>
 __global__ void __launch_bounds__(NT, GR_BFS_MIN_BLOCKS) bfs_persistent(BfsArgs a) {
   GridScope sc{a.ctl, a.status, a.spin, (int64_t)blockIdx.x * NT + threadIdx.x,
                (int64_t)gridDim.x * NT, 0u};
   __shared__ GrArena ar;
-  gr_bfs_body(a, sc, ar);
+  gr_bfs_body<PULL>(a, sc, ar);
+}
+
+const void* bfs_kernel(const BfsArgs& a) {
+  return a.use_do || a.force_pull ? (const void*)bfs_persistent<true>
+                                  : (const void*)bfs_persistent<false>;
 }
 
 #ifndef GR_BFS_CARVEOUT
@@ -51,8 +61,9 @@ void bfs_carveout_once() {
 #if GR_BFS_CARVEOUT >= 0
   static std::once_flag once;
   std::call_once(once, [] {
-    (void)cudaFuncSetAttribute((const void*)bfs_persistent,
-                               cudaFuncAttributePreferredSharedMemoryCarveout, GR_BFS_CARVEOUT);
+    for (const void* k : {(const void*)bfs_persistent<true>, (const void*)bfs_persistent<false>})
+      (void)cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 GR_BFS_CARVEOUT);
     (void)cudaGetLastError();
   });
 #endif
@@ -127,14 +138,13 @@ extern "C" gr_status gr_bfs(const gr_graph* g, int32_t src, int32_t* depth, int3
   a.pdef = ws->pdef;
 
   bfs_carveout_once();
-  int blocks = gr_launch_blocks((const void*)bfs_persistent, NT, 0, g->num_sms,
-                                o.blocks_per_sm);
+  const void* kernel = bfs_kernel(a);
+  int blocks = gr_launch_blocks(kernel, NT, 0, g->num_sms, o.blocks_per_sm);
   if (blocks <= 0) return GR_ERR_CUDA;
   if (o.max_blocks > 0 && blocks > o.max_blocks) blocks = o.max_blocks;
   if (gr_reset_ctl(ws, s) != cudaSuccess) return GR_ERR_CUDA;
   void* args[] = {&a};
-  if (cudaLaunchCooperativeKernel((const void*)bfs_persistent, dim3(blocks), dim3(NT), args, 0,
-                                  s) != cudaSuccess) {
+  if (cudaLaunchCooperativeKernel(kernel, dim3(blocks), dim3(NT), args, 0, s) != cudaSuccess) {
     (void)cudaGetLastError();
     return GR_ERR_CUDA;
   }
@@ -196,7 +206,7 @@ static __device__ __align__(256) unsigned char g_bfs_static_scratch[kStaticBytes
 struct StaticDevice {
   bool ready;
   unsigned char* base;  // device address of g_bfs_static_scratch
-  int blocks;           // co-resident grid size for bfs_persistent
+  int blocks[2];        // co-resident grid sizes of bfs_persistent<false>, <true>
 };
 constexpr int kMaxDevices = 64;
 StaticDevice g_static_dev[kMaxDevices];
@@ -216,10 +226,12 @@ gr_status static_setup(int device, StaticDevice** out) {
       (void)cudaGetLastError();
       return GR_ERR_CUDA;
     }
-    const int blocks = gr_launch_blocks((const void*)bfs_persistent, NT, 0, sms, 0);
-    if (blocks <= 0) return GR_ERR_CUDA;
+    const int b0 = gr_launch_blocks((const void*)bfs_persistent<false>, NT, 0, sms, 0);
+    const int b1 = gr_launch_blocks((const void*)bfs_persistent<true>, NT, 0, sms, 0);
+    if (b0 <= 0 || b1 <= 0) return GR_ERR_CUDA;
     d.base = (unsigned char*)p;
-    d.blocks = blocks;
+    d.blocks[0] = b0;
+    d.blocks[1] = b1;
     d.ready = true;
   }
   *out = &d;
@@ -284,8 +296,8 @@ extern "C" gr_status gr_bfs_static(int32_t n, int64_t m, const int32_t* row_offs
     return GR_ERR_CUDA;
   }
   void* args[] = {&a};
-  if (cudaLaunchCooperativeKernel((const void*)bfs_persistent, dim3(d->blocks), dim3(NT), args,
-                                  0, s) != cudaSuccess) {
+  if (cudaLaunchCooperativeKernel(bfs_kernel(a), dim3(d->blocks[a.use_do ? 1 : 0]), dim3(NT),
+                                  args, 0, s) != cudaSuccess) {
     (void)cudaGetLastError();
     return GR_ERR_CUDA;
   }

@@ -66,7 +66,9 @@ struct BfsArgs {
 // of a scope S: S::tid / S::nthreads index the participating threads, and
 // S::sync() is the step barrier (a bounded grid barrier for the cooperative
 // single-query kernel, the hardware cluster barrier for batched jobs).
-template <class S>
+// PULL = false compiles a push-only BFS: no pull levels and none of their
+// code (a.use_do and a.force_pull must then be 0).
+template <bool PULL, class S>
 __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar) {
   const int lane = threadIdx.x & 31;
   const int64_t gtid = sc.tid;
@@ -142,7 +144,7 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
       s_nbig = __ldcg(&ctl->nbig[s0]);
       s_mf = __ldcg(&ctl->mf[s0]);
       s_nu = __ldcg(&ctl->ulen[s0]);
-      s_ndef = a.pdef && L > 0 ? __ldcg(&ctl->ndef[s2]) : 0;
+      s_ndef = PULL && a.pdef && L > 0 ? __ldcg(&ctl->ndef[s2]) : 0;
       stage.reset();
       mstage.reset();
       ustage.reset();
@@ -162,7 +164,7 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
     // unvisited list if nothing matched.  The list's length was written
     // before the last barrier and is read with the level's other counters,
     // so every warp takes the same branch.
-    if (s_ndef > 0) {
+    if (PULL && s_ndef > 0) {
       {
         const int nd = min(s_ndef, GR_PULL_DEFER_CAP);
         const uint32_t* fprev = a.front[s2];
@@ -238,7 +240,9 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
     const unsigned long long mu = (unsigned long long)a.m > seen_edges
                                       ? (unsigned long long)a.m - seen_edges
                                       : 0ull;
-    if (a.force_pull) {
+    if (!PULL) {
+      // push only
+    } else if (a.force_pull) {
       pull = 1;
     } else if (a.use_do) {  // Eq. 5 / Eq. 6 with exact m_f, m_u
       if (!pull && (double)mf > (double)mu * a.do_a) pull = 1;
@@ -483,12 +487,13 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
       // First frontier neighbour in row order of each lane's candidate, or -1.
       // Each lane scans its first GR_PULL_SERIAL neighbours alone (rows are
       // sorted, so hubs come first and most candidates stop early); longer
-      // rows that still need more are then scanned by the whole warp, 128
-      // neighbours a round; a row still unresolved after GR_PULL_WARP_EDGES
-      // more, with GR_PULL_DEFER_MIN or more left, goes to the deferred list
-      // (GR_PULL_DEFERRED), which every warp of the grid finishes at the top
-      // of the next level.  v and vdeg are the candidate and its full
-      // degree.  All 32 lanes call.
+      // rows that still need more are then scanned by the whole warp, 32
+      // neighbours a round (four loads a lane in flight measured slower: most
+      // such rows stop in the first rounds); a row still unresolved after
+      // GR_PULL_WARP_EDGES more, with GR_PULL_DEFER_MIN or more left, goes to
+      // the deferred list (GR_PULL_DEFERRED), which every warp of the grid
+      // finishes at the top of the next level.  v and vdeg are the candidate
+      // and its full degree.  All 32 lanes call.
       auto find_parent = [&](bool cand, int beg, int deg, int32_t v, int vdeg) -> int32_t {
         int32_t found = -1;
         const int p = cand ? min(deg, GR_PULL_SERIAL) : 0;
@@ -517,7 +522,7 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
           const int dl = __shfl_sync(GR_FULL_MASK, vdeg, l);
           int32_t f = -1;
           bool may_defer = a.pdef != nullptr;
-          for (int e0 = lb + GR_PULL_SERIAL; e0 < le; e0 += 128) {
+          for (int e0 = lb + GR_PULL_SERIAL; e0 < le; e0 += 32) {
             if (may_defer && e0 - lb >= GR_PULL_SERIAL + GR_PULL_WARP_EDGES &&
                 le - e0 >= GR_PULL_DEFER_MIN) {  // warp-uniform
               int slot = 0;
@@ -537,24 +542,15 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
               }
               may_defer = false;  // the list is full: this warp scans on
             }
-            // 128 neighbours a round, four loads per lane in flight; the
-            // first hit in row order is the lowest (j, lane)
-            int32_t u[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const int e = e0 + j * 32 + lane;
-              u[j] = e < le ? __ldg(a.C + e) : -1;
-              if (u[j] >= 0) ++cnt.edges;
+            const int e = e0 + lane;
+            const bool ok = e < le;
+            const int32_t u = ok ? __ldg(a.C + e) : 0;
+            if (ok) ++cnt.edges;
+            const unsigned hm = __ballot_sync(GR_FULL_MASK, ok && ((fcur[u >> 5] >> (u & 31)) & 1u));
+            if (hm) {
+              f = __shfl_sync(GR_FULL_MASK, u, __ffs(hm) - 1);
+              break;
             }
-            bool in[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) in[j] = u[j] >= 0 && ((fcur[u[j] >> 5] >> (u[j] & 31)) & 1u);
-#pragma unroll
-            for (int j = 0; j < 4 && f < 0; ++j) {
-              const unsigned hm = __ballot_sync(GR_FULL_MASK, in[j]);
-              if (hm) f = __shfl_sync(GR_FULL_MASK, u[j], __ffs(hm) - 1);
-            }
-            if (f >= 0) break;
           }
           if (lane == l) found = f;
         }
