@@ -345,18 +345,29 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
       // is classified inside the edge loop.
       const int32_t* q = a.q[L & 1];
       const int2* ch = a.ch[L & 1];
-      auto pre = [&](bool active, int, int32_t v) -> uint32_t {
-        return active ? a.visited[v >> 5] : 0u;
+      // Both words of a target are read in the pre stage, before any mark of
+      // the round: the next-frontier word only for targets the visited
+      // bitmap lacks (skipping that load and marking blindly measured slower,
+      // 0.80 vs 0.68 ms on R-MAT s22 push-only, as duplicate red.or traffic
+      // to the same words outweighs the load).  Read in the mark stage
+      // instead, each load had to wait for the previous edge's red.or to the
+      // same bitmap, one L2 round trip per edge of the round.  Two edges of
+      // one lane's round to the same vertex may then both mark it: the
+      // reduction is idempotent and either predecessor is a valid parent.
+      struct VisNext {
+        uint32_t vis, next;
       };
-      auto mark = [&](bool active, int32_t u, uint32_t, int, int32_t v, uint32_t vis) {
+      auto pre = [&](bool active, int, int32_t v) -> VisNext {
+        const uint32_t b1 = 1u << (v & 31);
+        const uint32_t vis = active ? a.visited[v >> 5] : b1;
+        const uint32_t next = (vis & b1) ? b1 : __ldcg(fnext + (v >> 5));
+        return VisNext{vis, next};
+      };
+      auto mark = [&](bool active, int32_t u, uint32_t, int, int32_t v, const VisNext& w) {
         if (!active) return;
         ++cnt.edges;
         const uint32_t b1 = 1u << (v & 31);
-        // the next-frontier word is read only for targets the visited bitmap
-        // lacks; skipping that load and marking blindly measured slower
-        // (0.80 vs 0.68 ms on R-MAT s22 push-only), as duplicate red.or
-        // traffic to the same words outweighs the load
-        if (!(vis & b1) && !(__ldcg(fnext + (v >> 5)) & b1)) {
+        if (!(w.vis & b1) && !(w.next & b1)) {
           gr_red_or_u32(fnext + (v >> 5), b1);
           if (a.pred) a.pred[v] = u;
         }
