@@ -637,12 +637,21 @@ __device__ __forceinline__ void gr_rows_loop(const int32_t* list, int len, int p
 // GR_CHUNK_EDGES edges each, so they are dealt out statically (warp w takes
 // chunks w, w + nwarps, ...; no counter), and each warp prefetches two chunks
 // ahead: the entry of chunk c + 2 * nwarps and the row end and payload of
-// chunk c + nwarps are in flight while chunk c is expanded.
+// chunk c + nwarps are in flight while chunk c is expanded; with edge values
+// W (4-byte entries indexed like the columns) the columns and values of
+// chunk c + nwarps are also prefetched into L2, so that its expansion starts
+// from L2 instead of DRAM (1 % on R-MAT s22 SSSP; for column-only loops the
+// prefetch measured slower).
+__device__ __forceinline__ void gr_prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 template <int U, class Payload, class Pre, class Edge>
 __device__ __forceinline__ void gr_chunks_loop(const int2* ch, int nch, int swarp, int nwarps,
                                                int lane, const int32_t* __restrict__ R,
                                                const int32_t* __restrict__ C, GrCounters& cnt,
-                                               Payload&& payload, Pre&& pre, Edge&& edge) {
+                                               Payload&& payload, Pre&& pre, Edge&& edge,
+                                               const uint32_t* __restrict__ W = nullptr) {
+  static_assert(GR_CHUNK_EDGES <= 256, "nine 128-byte lines cover a chunk");
   int c = swarp;
   if (c >= nch) return;
   int2 cur = __ldcg(ch + c);
@@ -657,6 +666,10 @@ __device__ __forceinline__ void gr_chunks_loop(const int2* ch, int nch, int swar
     if (cn < nch) {
       nxt_end = min(nxt.y + GR_CHUNK_EDGES, __ldg(R + nxt.x + 1));
       nxt_pl = payload(nxt.x);
+      // lanes 0-8: the chunk's column lines, lanes 16-24: its W lines
+      const int pe = nxt.y + (lane & 15) * 32;
+      if (W && (lane & 15) < 9 && pe < nxt_end)
+        gr_prefetch_l2(lane < 16 ? (const void*)(C + pe) : (const void*)(W + pe));
     }
     if (lane == 0) ++cnt.verts;
     gr_warp_chunk_u<U>(C, cur.x, cur.y, cur_end, cur_pl, lane, pre, edge);

@@ -257,7 +257,7 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
       // largest work first: chunks, medium rows, then short rows
       auto label = [&](int32_t u) -> uint32_t { return (uint32_t)(__ldcg(a.key + u) >> 32); };
       gr_chunks_loop<GR_BULK_STRIPS>(ch, nch, swarp, (int)nwarps, lane, a.R, a.C,
-                                     cnt, label, pre, relax);
+                                     cnt, label, pre, relax, a.W);
       if (a.qm[0])
         gr_rows_loop<GR_BULK_STRIPS>(a.qm[it & 1], nqm, GR_MEDIUM_BATCH, &ctl->workm[s0], swarp,
                                      (int)nwarps, lane, a.R, a.C, cnt, label, pre, relax);
@@ -365,7 +365,7 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
       // warps never touch)
       auto label = [&](int32_t u) -> uint32_t { return (uint32_t)(a.key[u] >> 32); };
       gr_chunks_loop<GR_RELAX_STRIPS>(ch, nch, swarp, (int)nwarps, lane, a.R, a.C,
-                                      cnt, label, pre, relax);
+                                      cnt, label, pre, relax, a.W);
       if (a.qm[0])
         gr_rows_loop<GR_RELAX_STRIPS>(a.qm[it & 1], nqm, GR_MEDIUM_BATCH, &ctl->workm[s0], swarp,
                                       (int)nwarps, lane, a.R, a.C, cnt, label, pre, relax);
