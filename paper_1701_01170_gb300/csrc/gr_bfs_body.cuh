@@ -101,16 +101,16 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
       a.front[2][w] = 0u;
     }
   }
-  if (gtid == 0) {
-    int beg = a.R[a.src], deg = a.R[a.src + 1] - beg;
-    if (a.track_deg && deg >= a.big)
-      gr_register_chunks(a.ch[0], a.chunk_cap, &ctl->nchunk[0], &ctl->nbig[0], a.src, beg, deg,
-                         a.status);
-    else {
+  {
+    const int beg = __ldg(a.R + a.src), deg = __ldg(a.R + a.src + 1) - beg;
+    if (a.track_deg && deg >= a.big) {
+      gr_register_source_chunks(a.ch[0], a.chunk_cap, &ctl->nchunk[0], &ctl->nbig[0], a.src,
+                                beg, deg, a.status, gtid, gthreads);
+    } else if (gtid == 0) {
       a.q[0][0] = a.src;
       ctl->qlen[0] = 1;
     }
-    ctl->mf[0] = (unsigned long long)deg;
+    if (gtid == 0) ctl->mf[0] = (unsigned long long)deg;
   }
   if (!sc.sync()) return;
 

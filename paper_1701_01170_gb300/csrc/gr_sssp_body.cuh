@@ -90,16 +90,17 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
   const int nwords = (int)(((int64_t)a.n + 31) >> 5);
   if (a.touched)
     for (int64_t w = gtid; w < nwords; w += gthreads) a.touched[w] = 0u;
-  if (gtid == 0) {
-    const int beg = a.R[a.src], deg = a.R[a.src + 1] - beg;
-    if (a.track_deg && deg >= a.big)
-      gr_register_chunks(a.ch[0], a.chunk_cap, &ctl->nchunk[0], &ctl->nbig[0], a.src, beg, deg,
-                         a.status);
-    else {
+  {
+    const int beg = __ldg(a.R + a.src), deg = __ldg(a.R + a.src + 1) - beg;
+    if (a.track_deg && deg >= a.big) {
+      gr_register_source_chunks(a.ch[0], a.chunk_cap, &ctl->nchunk[0], &ctl->nbig[0], a.src,
+                                beg, deg, a.status, gtid, gthreads);
+    } else if (gtid == 0) {
       a.q[0][0] = a.src;
       ctl->qlen[0] = 1;
     }
-    for (int k = 0; k < 3; ++k) ctl->farmin[k] = UINT_MAX;
+    if (gtid == 0)
+      for (int k = 0; k < 3; ++k) ctl->farmin[k] = UINT_MAX;
   }
   if (!sc.sync()) return;
 
