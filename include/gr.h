@@ -325,7 +325,7 @@ typedef struct gr_bfs_opts {
                             pass over that bitmap writes the depths and
                             builds the next frontier; smaller push levels
                             claim each target with an atomic as they go.
-                            0 = default (n / 8, at least 65536), < 0 =
+                            0 = default (2 n, at least 65536), < 0 =
                             never.  Results do not depend on it             */
 } gr_bfs_opts;
 
