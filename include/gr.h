@@ -361,7 +361,8 @@ typedef struct gr_sssp_opts {
                             bulk: atomics without return values plus a
                             label-change bitmap, then one pass over the bitmap
                             builds the next piles; smaller ones enqueue per
-                            edge.  0 = default (n / 64, at least 4096),
+                            edge.  0 = default: 64 on a graph with a row of
+                            1024 or more edges, else n / 64 (at least 4096);
                             < 0 = never                                      */
   int32_t max_blocks;    /* as in gr_bfs_opts                                  */
   int32_t levels;        /* buckets of the priority queue (Sec. 5.1.5): 0 =

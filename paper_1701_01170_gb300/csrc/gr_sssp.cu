@@ -105,7 +105,9 @@ extern "C" gr_status gr_sssp(const gr_graph* g, int32_t src, uint32_t* dist, int
   a.stamp_near = ws->stamp_near;
   a.stamp_far = ws->stamp_far;
   a.touched = o.bulk_rows < 0 ? nullptr : ws->visited;  // the BFS bitmap is free here
-  a.bulk_rows = o.bulk_rows > 0 ? o.bulk_rows : gr_default_bulk_rows(g->n);
+  a.bulk_rows = o.bulk_rows > 0 ? o.bulk_rows
+                 : g->max_degree >= GR_SKEWED_DEGREE ? GR_SKEWED_BULK_ROWS
+                                                     : gr_default_bulk_rows(g->n);
   a.ctl = ws->ctl;
   a.status = ws->status;
   a.src = src;
