@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(BT) batch_kernel(BatchArgs b, SlotLayout L) {
       a.big = J.big;
       a.track_deg = J.max_degree >= GR_MEDIUM_DEGREE;
       a.spin = b.spin;
-      gr_sssp_body(a, sc, ar);
+      gr_sssp_body<false>(a, sc, ar);
     }
     cluster_barrier();  // the job is complete before rank 0 reuses the slot
   }

@@ -453,25 +453,38 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
       // (a few rows with many edges count as large: their targets repeat)
       const bool direct_claim =
           nf < GR_DIRECT_CLAIM_FRONTIER && (!a.track_deg || mf < 2ull * GR_DIRECT_CLAIM_FRONTIER);
-      // pass 2 of the multi-strip expansion: the visited word of each target
-      auto pre = [&](bool active, int, int32_t v) -> uint32_t {
-        return (active && !direct_claim) ? a.visited[v >> 5] : 0u;
+      // Stages of the multi-strip expansion, each for all strips of a round
+      // before the next: the visited word of each target (pre), the claims
+      // (atomics with return values, all in flight together), the row bounds
+      // of the targets won, then the writes and appends (visit).
+      struct Claim {
+        uint32_t word;
+        int32_t won;
+        int32_t vbeg, vdeg;
       };
-      auto visit = [&](bool active, int32_t u, uint32_t, int, int32_t v, uint32_t word) {
+      auto pre = [&](bool active, int, int32_t v) -> Claim {
+        return Claim{(active && !direct_claim) ? a.visited[v >> 5] : 0u, 0, 0, 0};
+      };
+      auto claim = [&](bool active, int32_t, uint32_t, int, int32_t v, Claim& c) {
+        const bool try_claim = active && (direct_claim || !(c.word & (1u << (v & 31))));
+        c.won = gr_warp_claim(a.visited, try_claim, v, lane);
+      };
+      auto bounds = [&](bool, int32_t, uint32_t, int, int32_t v, Claim& c) {
+        if (c.won && a.track_deg) {
+          c.vbeg = __ldg(a.R + v);
+          c.vdeg = __ldg(a.R + v + 1) - c.vbeg;
+        }
+      };
+      auto visit = [&](bool active, int32_t u, uint32_t, int, int32_t v, const Claim& c) {
         if (active) ++cnt.edges;
-        const bool try_claim = active && (direct_claim || !(word & (1u << (v & 31))));
-        const bool won = gr_warp_claim(a.visited, try_claim, v, lane);
+        const bool won = c.won;
         if (a.use_do) gr_warp_set_bit(fnext, won, v, lane);
-        int vbeg = 0, vdeg = 0;
+        const int vbeg = c.vbeg, vdeg = c.vdeg;
         if (won) {
           ++cnt.updates;
           a.depth[v] = next_depth;
           if (a.pred) a.pred[v] = u;
-          if (a.track_deg) {
-            vbeg = __ldg(a.R + v);
-            vdeg = __ldg(a.R + v + 1) - vbeg;
-            my_mf += (unsigned long long)vdeg;
-          }
+          my_mf += (unsigned long long)vdeg;
         }
         const bool big = won && vdeg >= a.big;
         const bool mid = won && !big && qmn && vdeg >= GR_MEDIUM_DEGREE;
@@ -485,13 +498,14 @@ __device__ __forceinline__ void gr_bfs_body(const BfsArgs& a, S& sc, GrArena& ar
       // then short rows 32 at a time (first batch by warp index, further
       // batches from a counter that idle warps never touch)
       auto no_payload = [](int32_t) -> uint32_t { return 0u; };
-      gr_chunks_loop<GR_VISIT_STRIPS>(ch, nch, swarp, (int)nwarps, lane, a.R, a.C,
-                                      cnt, no_payload, pre, visit);
+      gr_chunks_loop_mid<GR_VISIT_STRIPS>(ch, nch, swarp, (int)nwarps, lane, a.R, a.C, cnt,
+                                          no_payload, pre, claim, bounds, visit);
       if (a.qm[0])
-        gr_rows_loop<GR_VISIT_STRIPS>(a.qm[L & 1], nqm, GR_MEDIUM_BATCH, &ctl->workm[s0], swarp,
-                                      (int)nwarps, lane, a.R, a.C, cnt, no_payload, pre, visit);
-      gr_rows_loop<GR_VISIT_STRIPS>(q, nq, 32, &ctl->work[s0], swarp, (int)nwarps, lane, a.R, a.C,
-                                    cnt, no_payload, pre, visit);
+        gr_rows_loop_mid<GR_VISIT_STRIPS>(a.qm[L & 1], nqm, GR_MEDIUM_BATCH, &ctl->workm[s0],
+                                          swarp, (int)nwarps, lane, a.R, a.C, cnt, no_payload,
+                                          pre, claim, bounds, visit);
+      gr_rows_loop_mid<GR_VISIT_STRIPS>(q, nq, 32, &ctl->work[s0], swarp, (int)nwarps, lane,
+                                        a.R, a.C, cnt, no_payload, pre, claim, bounds, visit);
     } else {
       // ---- pull: unvisited vertices look for a parent in the frontier ----
       // (Alg. 2 Reverse_Advance: the step yields the next active frontier and

@@ -545,12 +545,18 @@ __device__ __forceinline__ void gr_warp_expand(const int32_t* __restrict__ R,
 // `pre(active, e, v)`
 // issues the per-edge loads the functor needs (its results are returned),
 // and only then `edge(active, src, payload, e, v, pre_value)` runs for each
-// strip.  All lanes call both functors.
-template <int U, class Pre, class Edge>
-__device__ __forceinline__ void gr_warp_expand_u(const int32_t* __restrict__ R,
-                                                 const int32_t* __restrict__ C, bool valid,
-                                                 int32_t u, int beg, int deg, uint32_t payload,
-                                                 int lane, Pre&& pre, Edge&& edge) {
+// strip.  All lanes call both functors.  The _mid form runs two more stages
+// in between, each for all U strips before the next: `mid1` and `mid2`, with
+// the arguments of `edge` and the pre value by reference.  Atomics whose results a
+// later stage needs, and loads that depend on those results, are then in
+// flight for all strips together; issued from `edge` they would wait strip
+// by strip (the compiler keeps them in program order).
+template <int U, class Pre, class Mid1, class Mid2, class Edge>
+__device__ __forceinline__ void gr_warp_expand_mid_u(const int32_t* __restrict__ R,
+                                                     const int32_t* __restrict__ C, bool valid,
+                                                     int32_t u, int beg, int deg,
+                                                     uint32_t payload, int lane, Pre&& pre,
+                                                     Mid1&& mid1, Mid2&& mid2, Edge&& edge) {
   if (!valid) deg = 0;
   int total;
   const int off = gr_warp_excl_scan(deg, lane, &total);
@@ -580,15 +586,35 @@ __device__ __forceinline__ void gr_warp_expand_u(const int32_t* __restrict__ R,
 #pragma unroll
     for (int k = 0; k < U; ++k) pv[k] = pre(act[k], e[k], v[k]);
 #pragma unroll
+    for (int k = 0; k < U; ++k) mid1(act[k], su[k], sp[k], e[k], v[k], pv[k]);
+#pragma unroll
+    for (int k = 0; k < U; ++k) mid2(act[k], su[k], sp[k], e[k], v[k], pv[k]);
+#pragma unroll
     for (int k = 0; k < U; ++k) edge(act[k], su[k], sp[k], e[k], v[k], pv[k]);
   }
 }
 
-// Chunk counterpart of gr_warp_expand_u: edges [e0, e1) of row u.
+struct GrNoMid {
+  template <class P>
+  __device__ __forceinline__ void operator()(bool, int32_t, uint32_t, int, int32_t, P&) const {}
+};
+
 template <int U, class Pre, class Edge>
-__device__ __forceinline__ void gr_warp_chunk_u(const int32_t* __restrict__ C, int32_t u, int e0,
-                                                int e1, uint32_t payload, int lane, Pre&& pre,
-                                                Edge&& edge) {
+__device__ __forceinline__ void gr_warp_expand_u(const int32_t* __restrict__ R,
+                                                 const int32_t* __restrict__ C, bool valid,
+                                                 int32_t u, int beg, int deg, uint32_t payload,
+                                                 int lane, Pre&& pre, Edge&& edge) {
+  gr_warp_expand_mid_u<U>(R, C, valid, u, beg, deg, payload, lane, pre, GrNoMid{}, GrNoMid{},
+                          edge);
+}
+
+// Chunk counterpart of gr_warp_expand_mid_u / gr_warp_expand_u: edges
+// [e0, e1) of row u.
+template <int U, class Pre, class Mid1, class Mid2, class Edge>
+__device__ __forceinline__ void gr_warp_chunk_mid_u(const int32_t* __restrict__ C, int32_t u,
+                                                    int e0, int e1, uint32_t payload, int lane,
+                                                    Pre&& pre, Mid1&& mid1, Mid2&& mid2,
+                                                    Edge&& edge) {
   for (int base = e0; base < e1; base += 32 * U) {
     int e[U], v[U];
     bool act[U];
@@ -602,19 +628,31 @@ __device__ __forceinline__ void gr_warp_chunk_u(const int32_t* __restrict__ C, i
 #pragma unroll
     for (int k = 0; k < U; ++k) pv[k] = pre(act[k], e[k], v[k]);
 #pragma unroll
+    for (int k = 0; k < U; ++k) mid1(act[k], u, payload, e[k], v[k], pv[k]);
+#pragma unroll
+    for (int k = 0; k < U; ++k) mid2(act[k], u, payload, e[k], v[k], pv[k]);
+#pragma unroll
     for (int k = 0; k < U; ++k) edge(act[k], u, payload, e[k], v[k], pv[k]);
   }
 }
 
+template <int U, class Pre, class Edge>
+__device__ __forceinline__ void gr_warp_chunk_u(const int32_t* __restrict__ C, int32_t u, int e0,
+                                                int e1, uint32_t payload, int lane, Pre&& pre,
+                                                Edge&& edge) {
+  gr_warp_chunk_mid_u<U>(C, u, e0, e1, payload, lane, pre, GrNoMid{}, GrNoMid{}, edge);
+}
+
 // Static-first / dynamic loop over a row list, `per` rows per warp batch,
-// each batch expanded with gr_warp_expand_u<U>; payload(u) gives the value
-// passed to the edge functor with every edge of row u.
-template <int U, class Payload, class Pre, class Edge>
-__device__ __forceinline__ void gr_rows_loop(const int32_t* list, int len, int per, int* counter,
-                                             int swarp, int nwarps, int lane,
-                                             const int32_t* __restrict__ R,
-                                             const int32_t* __restrict__ C, GrCounters& cnt,
-                                             Payload&& payload, Pre&& pre, Edge&& edge) {
+// each batch expanded with gr_warp_expand_mid_u<U>; payload(u) gives the
+// value passed to the edge functor with every edge of row u.
+template <int U, class Payload, class Pre, class Mid1, class Mid2, class Edge>
+__device__ __forceinline__ void gr_rows_loop_mid(const int32_t* list, int len, int per,
+                                                 int* counter, int swarp, int nwarps, int lane,
+                                                 const int32_t* __restrict__ R,
+                                                 const int32_t* __restrict__ C, GrCounters& cnt,
+                                                 Payload&& payload, Pre&& pre, Mid1&& mid1,
+                                                 Mid2&& mid2, Edge&& edge) {
   for (int base = swarp * per; base < len;
        base = gr_next_batch(base, len, nwarps * per, counter, per, lane)) {
     const int i = base + lane;
@@ -629,8 +667,18 @@ __device__ __forceinline__ void gr_rows_loop(const int32_t* list, int len, int p
       deg = __ldg(R + u + 1) - beg;
       pl = payload(u);
     }
-    gr_warp_expand_u<U>(R, C, valid, u, beg, deg, pl, lane, pre, edge);
+    gr_warp_expand_mid_u<U>(R, C, valid, u, beg, deg, pl, lane, pre, mid1, mid2, edge);
   }
+}
+
+template <int U, class Payload, class Pre, class Edge>
+__device__ __forceinline__ void gr_rows_loop(const int32_t* list, int len, int per, int* counter,
+                                             int swarp, int nwarps, int lane,
+                                             const int32_t* __restrict__ R,
+                                             const int32_t* __restrict__ C, GrCounters& cnt,
+                                             Payload&& payload, Pre&& pre, Edge&& edge) {
+  gr_rows_loop_mid<U>(list, len, per, counter, swarp, nwarps, lane, R, C, cnt, payload, pre,
+                      GrNoMid{}, GrNoMid{}, edge);
 }
 
 // Loop over the edge chunks of split rows.  Chunks hold at most
@@ -645,12 +693,15 @@ __device__ __forceinline__ void gr_rows_loop(const int32_t* list, int len, int p
 __device__ __forceinline__ void gr_prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
-template <int U, class Payload, class Pre, class Edge>
-__device__ __forceinline__ void gr_chunks_loop(const int2* ch, int nch, int swarp, int nwarps,
-                                               int lane, const int32_t* __restrict__ R,
-                                               const int32_t* __restrict__ C, GrCounters& cnt,
-                                               Payload&& payload, Pre&& pre, Edge&& edge,
-                                               const uint32_t* __restrict__ W = nullptr) {
+template <int U, class Payload, class Pre, class Mid1, class Mid2, class Edge>
+__device__ __forceinline__ void gr_chunks_loop_mid(const int2* ch, int nch, int swarp,
+                                                   int nwarps, int lane,
+                                                   const int32_t* __restrict__ R,
+                                                   const int32_t* __restrict__ C,
+                                                   GrCounters& cnt, Payload&& payload,
+                                                   Pre&& pre, Mid1&& mid1, Mid2&& mid2,
+                                                   Edge&& edge,
+                                                   const uint32_t* __restrict__ W = nullptr) {
   static_assert(GR_CHUNK_EDGES <= 256, "nine 128-byte lines cover a chunk");
   int c = swarp;
   if (c >= nch) return;
@@ -672,12 +723,22 @@ __device__ __forceinline__ void gr_chunks_loop(const int2* ch, int nch, int swar
         gr_prefetch_l2(lane < 16 ? (const void*)(C + pe) : (const void*)(W + pe));
     }
     if (lane == 0) ++cnt.verts;
-    gr_warp_chunk_u<U>(C, cur.x, cur.y, cur_end, cur_pl, lane, pre, edge);
+    gr_warp_chunk_mid_u<U>(C, cur.x, cur.y, cur_end, cur_pl, lane, pre, mid1, mid2, edge);
     cur = nxt;
     cur_end = nxt_end;
     cur_pl = nxt_pl;
     nxt = nn;
   }
+}
+
+template <int U, class Payload, class Pre, class Edge>
+__device__ __forceinline__ void gr_chunks_loop(const int2* ch, int nch, int swarp, int nwarps,
+                                               int lane, const int32_t* __restrict__ R,
+                                               const int32_t* __restrict__ C, GrCounters& cnt,
+                                               Payload&& payload, Pre&& pre, Edge&& edge,
+                                               const uint32_t* __restrict__ W = nullptr) {
+  gr_chunks_loop_mid<U>(ch, nch, swarp, nwarps, lane, R, C, cnt, payload, pre, GrNoMid{},
+                        GrNoMid{}, edge, W);
 }
 
 // Default SSSP bucket width: 256 * mean weight / mean degree (at least 1).

@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(NT, GR_SSSP_MIN_BLOCKS) sssp_persistent(SsspAr
                (int64_t)gridDim.x * NT, 0u};
   __shared__ GrArena ar;
   extern __shared__ GrStageBufs big[];  // one CTA per SM: room for large staging buffers
-  gr_sssp_body(a, sc, ar, GR_SSSP_BIG_STAGE ? big : nullptr);
+  gr_sssp_body<NT == NT_NARROW>(a, sc, ar, GR_SSSP_BIG_STAGE ? big : nullptr);
 }
 
 }  // namespace

@@ -75,7 +75,12 @@ struct SsspArgs {
 
 constexpr unsigned long long GR_KEY_INF = ~0ull;
 
-template <class S>
+// STAGED selects the staged per-edge RELAX (atomics and dependent loads of all
+// strips of a round in flight together): 11 % faster on the 4096^2 grid,
+// whose small steps all take that path, but 3 % slower on R-MAT s22 through
+// the register allocation of its bulk steps, so only the mesh instantiation
+// uses it.
+template <bool STAGED, class S>
 __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& ar,
                                              GrStageBufs* big = nullptr) {
   const int lane = threadIdx.x & 31;
@@ -335,26 +340,36 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
       // ---- RELAX: advance + Update_Label / Set_Pred + Remove_Redundant ----
       const int32_t* q = a.q[it & 1];
       const int2* ch = a.ch[it & 1];
-      // pass 2: weight and current key of each edge's target
-      struct Pre {
-        uint32_t w;
-        unsigned long long cur;
-      };
-      auto pre = [&](bool active, int e, int32_t v) -> Pre {
-        Pre p{0u, 0ull};
-        if (active) {
-          p.w = GR_LDSTREAM(a.W + e);
-          p.cur = a.key[v];
-        }
-        return p;
-      };
-      // pass 3: Update_Label / Set_Pred as one 64-bit atomicMin on the key
-      auto relax = [&](bool active, int32_t u, uint32_t du, int, int32_t v, const Pre& p) {
-        bool imp = false;
-        unsigned long long nd = 0;
-        if (active) {
+      if (STAGED) {
+        // Stages, each for all strips of a round before the next (every result
+        // is examined one stage after its atomic or load was issued, so the
+        // strips' round trips overlap):
+        //  pre: weight and current key of each edge's target;
+        //  tryk: Update_Label / Set_Pred as one 64-bit atomicMin on the key for
+        //    candidates below the current key, and the target's row bounds
+        //    (used if it joins the near frontier);
+        //  stamp: for targets whose label this edge lowered below T, the
+        //    near-frontier stamp exchange (joins once per step);
+        //  relax: the appends.
+        struct Pre {
+          uint32_t w;
+          uint32_t stamp;           // previous near stamp (when exchanged)
+          unsigned long long key;   // current key, then the atomicMin's return value
+          int32_t vbeg, vdeg;
+          int32_t tried;            // an atomicMin was issued
+        };
+        auto pre = [&](bool active, int e, int32_t v) -> Pre {
+          Pre p{0u, 0u, 0ull, 0, 0, 0};
+          if (active) {
+            p.w = GR_LDSTREAM(a.W + e);
+            p.key = a.key[v];
+          }
+          return p;
+        };
+        auto tryk = [&](bool active, int32_t u, uint32_t du, int, int32_t v, Pre& p) {
+          if (!active) return;
           ++cnt.edges;
-          nd = (unsigned long long)du + p.w;
+          const unsigned long long nd = (unsigned long long)du + p.w;
           if (nd >= (unsigned long long)GR_INF_DIST) {
             // not representable: drop the candidate; whether a true distance
             // overflows is decided after convergence
@@ -362,26 +377,93 @@ __device__ __forceinline__ void gr_sssp_body(const SsspArgs& a, S& sc, GrArena& 
               ovf_seen = true;
               atomicExch(&ctl->ovf_pending, 1);
             }
-          } else {
-            const unsigned long long cand = (nd << 32) | (unsigned)u;
-            if (cand < p.cur) imp = (atomicMin(&a.key[v], cand) >> 32) > nd;
-            cnt.updates += imp;
+            return;
           }
-        }
-        to_near(imp && nd < T, v);
-        to_far(imp && nd >= T, v, (unsigned)nd, fe);
-      };
-      // largest work first: chunks, medium rows, then short rows 32 at a time
-      // (first batch by warp index, further batches from a counter that idle
-      // warps never touch)
-      auto label = [&](int32_t u) -> uint32_t { return (uint32_t)(a.key[u] >> 32); };
-      gr_chunks_loop<GR_RELAX_STRIPS>(ch, nch, swarp, (int)nwarps, lane, a.R, a.C,
-                                      cnt, label, pre, relax, a.W);
-      if (a.qm[0])
-        gr_rows_loop<GR_RELAX_STRIPS>(a.qm[it & 1], nqm, GR_MEDIUM_BATCH, &ctl->workm[s0], swarp,
-                                      (int)nwarps, lane, a.R, a.C, cnt, label, pre, relax);
-      gr_rows_loop<GR_RELAX_STRIPS>(q, nq, 32, &ctl->work[s0], swarp, (int)nwarps, lane, a.R, a.C,
-                                    cnt, label, pre, relax);
+          const unsigned long long cand = (nd << 32) | (unsigned)u;
+          if (cand < p.key) {
+            p.tried = 1;
+            p.key = atomicMin(&a.key[v], cand);
+            if (nd < T && a.track_deg) {
+              p.vbeg = __ldg(a.R + v);
+              p.vdeg = __ldg(a.R + v + 1) - p.vbeg;
+            }
+          }
+        };
+        auto improved = [&](uint32_t du, const Pre& p) {
+          return p.tried && (p.key >> 32) > (unsigned long long)du + p.w;
+        };
+        auto stamp = [&](bool, int32_t, uint32_t du, int, int32_t v, Pre& p) {
+          if (improved(du, p) && (unsigned long long)du + p.w < T)
+            p.stamp = (uint32_t)atomicExch(&a.stamp_near[v], next_stamp);
+        };
+        auto relax = [&](bool, int32_t, uint32_t du, int, int32_t v, const Pre& p) {
+          const bool imp = improved(du, p);
+          const unsigned long long nd = (unsigned long long)du + p.w;
+          cnt.updates += imp;
+          near_append_row(imp && nd < T && p.stamp != (uint32_t)next_stamp, v, p.vbeg, p.vdeg);
+          to_far(imp && nd >= T, v, (unsigned)nd, fe);
+        };
+        // largest work first: chunks, medium rows, then short rows 32 at a time
+        // (first batch by warp index, further batches from a counter that idle
+        // warps never touch)
+        auto label = [&](int32_t u) -> uint32_t { return (uint32_t)(a.key[u] >> 32); };
+        gr_chunks_loop_mid<GR_RELAX_STRIPS>(ch, nch, swarp, (int)nwarps, lane, a.R, a.C, cnt,
+                                            label, pre, tryk, stamp, relax, a.W);
+        if (a.qm[0])
+          gr_rows_loop_mid<GR_RELAX_STRIPS>(a.qm[it & 1], nqm, GR_MEDIUM_BATCH, &ctl->workm[s0],
+                                            swarp, (int)nwarps, lane, a.R, a.C, cnt, label, pre,
+                                            tryk, stamp, relax);
+        gr_rows_loop_mid<GR_RELAX_STRIPS>(q, nq, 32, &ctl->work[s0], swarp, (int)nwarps, lane,
+                                          a.R, a.C, cnt, label, pre, tryk, stamp, relax);
+      } else {
+        // pass 2: weight and current key of each edge's target
+        struct Pre {
+          uint32_t w;
+          unsigned long long cur;
+        };
+        auto pre = [&](bool active, int e, int32_t v) -> Pre {
+          Pre p{0u, 0ull};
+          if (active) {
+            p.w = GR_LDSTREAM(a.W + e);
+            p.cur = a.key[v];
+          }
+          return p;
+        };
+        // pass 3: Update_Label / Set_Pred as one 64-bit atomicMin on the key
+        auto relax = [&](bool active, int32_t u, uint32_t du, int, int32_t v, const Pre& p) {
+          bool imp = false;
+          unsigned long long nd = 0;
+          if (active) {
+            ++cnt.edges;
+            nd = (unsigned long long)du + p.w;
+            if (nd >= (unsigned long long)GR_INF_DIST) {
+              // not representable: drop the candidate; whether a true distance
+              // overflows is decided after convergence
+              if (!ovf_seen) {
+                ovf_seen = true;
+                atomicExch(&ctl->ovf_pending, 1);
+              }
+            } else {
+              const unsigned long long cand = (nd << 32) | (unsigned)u;
+              if (cand < p.cur) imp = (atomicMin(&a.key[v], cand) >> 32) > nd;
+              cnt.updates += imp;
+            }
+          }
+          to_near(imp && nd < T, v);
+          to_far(imp && nd >= T, v, (unsigned)nd, fe);
+        };
+        // largest work first: chunks, medium rows, then short rows 32 at a time
+        // (first batch by warp index, further batches from a counter that idle
+        // warps never touch)
+        auto label = [&](int32_t u) -> uint32_t { return (uint32_t)(a.key[u] >> 32); };
+        gr_chunks_loop<GR_RELAX_STRIPS>(ch, nch, swarp, (int)nwarps, lane, a.R, a.C,
+                                        cnt, label, pre, relax, a.W);
+        if (a.qm[0])
+          gr_rows_loop<GR_RELAX_STRIPS>(a.qm[it & 1], nqm, GR_MEDIUM_BATCH, &ctl->workm[s0], swarp,
+                                        (int)nwarps, lane, a.R, a.C, cnt, label, pre, relax);
+        gr_rows_loop<GR_RELAX_STRIPS>(q, nq, 32, &ctl->work[s0], swarp, (int)nwarps, lane, a.R, a.C,
+                                      cnt, label, pre, relax);
+      }
     } else if (a.ring[0] && big) {
       // ---- SPLIT with the multi-level queue (a multisplit of the far pile) --
       // Phase 1: every entry of the far pile (vertices that left the current
