@@ -68,7 +68,8 @@ class Dispatcher:
     served (reused), plus one multi-source scratch per graph.  A unit is
     admitted on an idle lane when the bytes it would add keep the total under
     `budget`; otherwise the lane evicts its own least recently used
-    workspaces first, and if that is not enough the unit waits.
+    workspaces first, then those of other idle lanes (nothing runs on them),
+    and if that is not enough the unit waits for running lanes to finish.
     """
 
     def __init__(self, graphs: dict[str, GraphInfo], lanes: int, budget: int,
@@ -89,10 +90,13 @@ class Dispatcher:
         gi = self.graphs[g]
         return gi.bytes_bfs if op == OP_BFS else gi.bytes_sssp
 
-    def admit(self, lane: int) -> tuple[Unit | None, list]:
-        """Next unit for an idle lane and the (graph, op) workspaces to evict first."""
+    def admit(self, lane: int, idle=()) -> tuple[Unit | None, list]:
+        """Next unit for an idle lane and the (lane, (graph, op)) workspaces to evict
+        first: the lane's own, least recently used first, then those of the other
+        lanes in `idle`."""
         if not self.pending:
             return None, []
+        others = [l for l in idle if l != lane]
         for idx, r in enumerate(self.pending):
             gi = self.graphs[r.graph]
             multi = r.op == OP_BFS and gi.multi_ok and r.graph not in self.multi_busy
@@ -103,17 +107,20 @@ class Dispatcher:
             evict = []
             free = self.budget - self.used
             if need > free:
-                for key, b in self.lane_ws[lane].items():   # least recently used first
-                    if key == (r.graph, r.op):
-                        continue
-                    evict.append(key)
-                    free += b
+                for l in [lane] + others:
+                    for key, b in self.lane_ws[l].items():   # least recently used first
+                        if l == lane and key == (r.graph, r.op):
+                            continue
+                        evict.append((l, key))
+                        free += b
+                        if need <= free:
+                            break
                     if need <= free:
                         break
                 if need > free:
                     continue                      # try a later request that fits
-            for key in evict:
-                self.used -= self.lane_ws[lane].pop(key)
+            for l, key in evict:
+                self.used -= self.lane_ws[l].pop(key)
                 self.evictions += 1
             if multi:
                 group = [r]
@@ -231,13 +238,14 @@ class GpuBackend:
         torch.cuda.synchronize()
 
     def evict(self, lane: int, keys):
-        """Release a lane's workspaces in the order of the lane's stream: the other lanes'
-        streams keep running (nothing waits for the whole device)."""
+        """Release workspaces, each in the order of the stream of the lane that holds it
+        (`keys` are (lane, (graph, op)) pairs): the other lanes' streams keep running
+        (nothing waits for the whole device)."""
         from . import gr_workspace_destroy_async
-        for key in keys:
-            ws = self.ws[lane].pop(key, None)
+        for l, key in keys:
+            ws = self.ws[l].pop(key, None)
             if ws:
-                gr_workspace_destroy_async(ws, self.streams[lane])
+                gr_workspace_destroy_async(ws, self.streams[l])
                 self.evicted += 1
 
     def _workspace(self, lane, graph, op):
@@ -327,19 +335,26 @@ def serve_trace(backend, trace: list[Request], lanes: int, budget: int, multi_na
                 disp.pending.append(trace[nxt])
                 nxt += 1
             started = False
-            while idle and disp.pending:
-                lane = idle[-1]
-                unit, evict = disp.admit(lane)
-                if unit is None:
+            progress = True
+            while idle and disp.pending and progress:
+                progress = False
+                for lane in reversed(idle):
+                    unit, evict = disp.admit(lane, idle)
+                    if unit is None:
+                        continue
+                    idle.remove(lane)
+                    backend.evict(lane, evict)
+                    th = threading.Thread(target=work, args=(lane, unit), daemon=True)
+                    th.start()
+                    threads.append(th)
+                    started = progress = True
                     break
-                idle.pop()
-                backend.evict(lane, evict)
-                th = threading.Thread(target=work, args=(lane, unit), daemon=True)
-                th.start()
-                threads.append(th)
-                started = True
             if started:
                 continue
+            if disp.pending and len(idle) == lanes:
+                # every lane is idle and nothing fits even after evicting all
+                # their workspaces: waiting cannot help
+                raise RuntimeError("serve_trace: a pending request exceeds the memory budget")
             wait = 0.05
             if nxt < len(trace):
                 wait = max(0.0, min(wait, trace[nxt].t_arrival - (time.perf_counter() - t0)))

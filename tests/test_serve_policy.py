@@ -43,8 +43,25 @@ def test_admission_respects_the_memory_budget_and_evicts_lru():
     u, ev = d.admit(0)
     assert u.requests[0].rid == 1 and d.used == 300 and not ev
     u, ev = d.admit(0)                    # needs 600: evicts a/BFS then a/SSSP
-    assert u.requests[0].rid == 2 and ev == [("a", OP_BFS), ("a", OP_SSSP)]
+    assert u.requests[0].rid == 2 and ev == [(0, ("a", OP_BFS)), (0, ("a", OP_SSSP))]
     assert d.used == 600 and d.evictions == 2
+
+
+def test_idle_lanes_workspaces_are_evicted_too():
+    # the budget is held by two lanes; a request that needs both lanes' memory is
+    # admitted only when the other lane is idle, and evicts the own lane's first
+    d = Dispatcher(infos(multi=()), lanes=2, budget=650)
+    d.pending.extend([req(0, "a", OP_SSSP), req(1, "b", OP_BFS), req(2, "b", OP_SSSP)])
+    u, _ = d.admit(0)
+    assert u.requests[0].rid == 0                 # lane 0 holds a/SSSP (200)
+    u, _ = d.admit(1)
+    assert u.requests[0].rid == 1                 # lane 1 holds b/BFS (300)
+    u, ev = d.admit(0, idle=[0])                  # lane 1 busy: 600 does not fit
+    assert u is None and d.used == 500
+    u, ev = d.admit(0, idle=[0, 1])
+    assert u.requests[0].rid == 2
+    assert ev == [(0, ("a", OP_SSSP)), (1, ("b", OP_BFS))]
+    assert d.used == 600 and not d.lane_ws[1]
 
 
 def test_request_that_cannot_fit_waits_while_others_proceed():
@@ -81,6 +98,25 @@ class FakeBackend:
             r.t_done = done
             r.result = (unit.graph, r.src)
         self.active -= 1
+
+
+def test_trace_completes_when_the_budget_is_spread_over_idle_lanes():
+    # two lanes end up holding one workspace each; the next request needs the
+    # memory of both (a dispatcher that lets a lane evict only its own
+    # workspaces waits for ever here, with every lane idle)
+    trace = [Request(0, "a", OP_SSSP, 0, 0.0), Request(1, "b", OP_BFS, 1, 0.0),
+             Request(2, "b", OP_SSSP, 2, 0.05)]
+    be = FakeBackend()
+    stats = serve_trace(be, trace, lanes=2, budget=650)
+    assert stats["completed"] == 3 and stats["errors"] == 0
+    assert all(r.result == (r.graph, r.src) for r in trace)
+
+
+def test_request_beyond_the_budget_is_an_error():
+    import pytest
+    trace = [Request(0, "b", OP_SSSP, 0, 0.0)]
+    with pytest.raises(RuntimeError):
+        serve_trace(FakeBackend(), trace, lanes=2, budget=500)
 
 
 def test_trace_completes_with_overlap_and_grouping():
