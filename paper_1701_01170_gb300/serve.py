@@ -302,7 +302,7 @@ class GpuBackend:
 
     def close(self):
         for lane in range(len(self.ws)):
-            self.evict(lane, list(self.ws[lane].keys()))
+            self.evict(lane, [(lane, k) for k in list(self.ws[lane].keys())])
         self.torch.cuda.synchronize()
 
 
