@@ -13,7 +13,17 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: large inputs; still part of the default run")
 
 
+# Upper bound on one test's wall time where pytest-timeout is installed (the
+# slowest test takes about 20 s): a test that stops making progress fails
+# after it instead of holding the run, and the GPU, until an outer limit.
+TEST_TIME_LIMIT_S = 600
+
+
 def pytest_collection_modifyitems(config, items):
+    if config.pluginmanager.hasplugin("timeout"):
+        for item in items:
+            if item.get_closest_marker("timeout") is None:
+                item.add_marker(pytest.mark.timeout(TEST_TIME_LIMIT_S))
     # GPU tests cannot run without a device; skip them loudly rather than fail on import.
     try:
         import torch
